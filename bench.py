@@ -1,0 +1,314 @@
+"""Benchmark: time-to-tolerance and stencil GLUP/s of the multisplitting solver.
+
+One step = one complete solve of the 256^3 Laplace workload (4x4x4 blocks of
+64^3, Dirichlet data iid U(-1,1) seed 2009, x0 = 0) to relative residual
+1e-8, FP32 inner CG / FP64 outer, synchronous block Jacobi -- every row of
+the hot path (residual with halo, inner CG, update, global norm and stop).
+Inputs are resident on the GPU before the timed region; the e2e figure goes
+through the host-buffer entry point (ms_solve_host) with the copies inside
+the timed region.
+
+value = stencil lattice updates (inner CG iterations x block points plus one
+residual pass per sweep) per second over the K timed solves, summed over
+ranks (N > 1: independent replicas, weak scaling).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-rel-residual-1e-8 and stencil GLUP/s vs plain FP64 sync; HBM GB/s vs peak"
+UNIT = "GLUP/s"
+WORKLOAD = "laplace256_u11"
+# algorithmic bytes per lattice update (roofline): the inner CG must
+# read and write r, p and d once per iteration (24 B at FP32, 48 B at FP64);
+# an outer sweep reads x (8 B) and writes r (4 B), then reads x and d and
+# writes x (20 B): 32 B per point at FP32 (the FP64 r/d add 8 B).
+INNER_BYTES = {"mixed": 24.0, "fp64": 48.0}
+OUTER_BYTES = {"mixed": 32.0, "fp64": 40.0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ms", choices=["ms", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--mode", default="sync", choices=["sync", "async"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP64-sync and async comparison solves")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [v.strip() for v in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = max(mx, float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        loaded = [v for v in sm if v >= 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle timing (CPU)
+def oracle_sample(cfg, sweeps, threads):
+    """Times `sweeps` outer sweeps of the FP64 CPU oracle on the full workload."""
+    import oracle
+    oracle.build()
+    oracle.set_threads(threads)
+    opts = dict(cfg["opts"])
+    t0 = time.perf_counter()
+    lups = 0
+    for s in range(cfg["nrhs"]):
+        r = oracle.solve(cfg["nx"], cfg["ny"], cfg["nz"], cfg["cx"], cfg["cy"], cfg["cz"], bnd=cfg["bnd"][s],
+                         inner_rtol=opts["inner_rtol"], inner_maxit=opts["inner_maxit"], outer_tol=0.0,
+                         outer_maxit=sweeps)
+        npts = cfg["nx"] * cfg["ny"] * cfg["nz"]
+        nblocks = (len(cfg["cx"]) - 1) * (len(cfg["cy"]) - 1) * (len(cfg["cz"]) - 1)
+        lups += (sweeps + 1) * npts + r["inner_its"] * (npts // nblocks)
+    el = time.perf_counter() - t0
+    return lups, el
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2009_12638_gb300 import inputs
+    import oracle
+    cfg = inputs.make_config(args.workload)
+    threads = oracle.max_threads()
+    sweeps = 1
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; warm-up steps are skipped deliberately
+    total_lups, total_s = 0, 0.0
+    for _ in range(args.steps):
+        lups, el = oracle_sample(cfg, sweeps, threads)
+        total_lups += lups
+        total_s += el
+    value = total_lups / total_s / 1e9
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": f"{args.workload}: 256^3, 4x4x4 blocks of 64^3, U(-1,1) "
+                                                        "boundary seed 2009, inner CG 50 its / rtol 1e-6"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                            "sample": f"{sweeps} outer sweep(s) of the full workload per step (FP64 CPU oracle, "
+                                      f"OpenMP over blocks)"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+
+    from paper_2009_12638_gb300 import Grid, inputs
+    cfg = inputs.make_config(args.workload)
+    # each rank solves its own replica (different boundary seed for rank > 0)
+    bnd_np = cfg["bnd"] if rank == 0 else inputs.boundary_uniform(cfg["nx"], cfg["ny"], cfg["nz"], cfg["nrhs"],
+                                                                   2009 + rank)
+    grid = Grid(cfg["nx"], cfg["ny"], cfg["nz"], cfg["nrhs"], device=dev)
+    grid.partition(len(cfg["cx"]) - 1, len(cfg["cy"]) - 1, len(cfg["cz"]) - 1, cfg["cx"], cfg["cy"], cfg["cz"])
+    bnd = torch.from_numpy(bnd_np).to(dev)
+    x = torch.zeros(grid.shape, dtype=torch.float64, device=dev)
+    opts = dict(cfg["opts"], precision=args.precision, mode=args.mode)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+    stream = torch.cuda.current_stream(dev)
+
+    def solve_once(**extra):
+        x.zero_()
+        return grid.solve(bnd=bnd, out=x, **dict(opts, **extra))
+
+    for _ in range(max(args.warmup, 3)):
+        _, st = solve_once()
+        assert st.status == 0, st
+    sampler = ClockSampler(local)
+    sampler.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    times, lups, launches, stats = [], 0, 0, []
+    for _ in range(args.steps):
+        flush.fill_(1.0)  # evict L2 between timed solves (not timed)
+        x.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, st = grid.solve(bnd=bnd, out=x, **opts)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        lups += st.lups
+        launches += st.launches
+        stats.append(st)
+        assert st.status == 0 and st.rel_residual < opts["outer_tol"], st
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    total_ms = sum(times)
+    t = torch.tensor([total_ms, float(lups)], dtype=torch.float64, device=dev)
+    if world > 1:
+        tmax = t.clone()
+        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        total_ms, lups_all = float(tmax[0]), float(t[1])
+    else:
+        lups_all = float(lups)
+    value = lups_all / (total_ms * 1e-3) / 1e9
+    st0 = stats[0]
+
+    # ---- end to end through the host-buffer entry point (pinned host memory)
+    xh = torch.zeros(grid.shape, dtype=torch.float64).pin_memory().numpy()
+    bh = torch.from_numpy(bnd_np.copy()).pin_memory().numpy()
+    grid.solve_host(bnd=bh, x=xh, **opts)  # warm the host-side workspace
+    e2e_ms, e2e_lups = 0.0, 0
+    for _ in range(args.steps):
+        xh[...] = 0.0
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        _, sh = grid.solve_host(bnd=bh, x=xh, **opts)
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+        e2e_lups += sh.lups
+        assert sh.status == 0
+    e2e_value = e2e_lups / (e2e_ms * 1e-3) / 1e9 * world
+
+    # ---- roofline of the dominant kernel (the sweep kernel), per-launch CUDA events
+    _, sp = solve_once(profile=True)
+    sweeps = sp.outer_its + 1
+    inner_lups = sp.lups - sweeps * grid.npts * grid.nrhs
+    alg_bytes = INNER_BYTES[args.precision] * inner_lups + OUTER_BYTES[args.precision] * sweeps * grid.npts
+    per_launch_ms = sp.sweep_ms / max(1, sp.sweep_launches)
+    achieved = alg_bytes / sweeps / (per_launch_ms * 1e-3) / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": f"sweep_kernel<{'float' if args.precision == 'mixed' else 'double'}>",
+                "per_launch_ms": per_launch_ms, "launches_timed": sp.sweep_launches,
+                "alg_bytes_per_launch": alg_bytes / sweeps,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s"}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
+           "data": "synthetic",
+           "config": {"workload": f"{args.workload}: 256^3 Laplace 7-point, 4x4x4 blocks of 64^3, boundary iid "
+                                  "U(-1,1) seed 2009, x0=0, inner CG <=50 its rtol 1e-6, outer rel tol 1e-8",
+                      "precision": args.precision, "mode": args.mode,
+                      "launch_shape": {"cluster": st0.cluster, "threads": st0.threads, "slots": st0.slots},
+                      "l2": "flushed (256 MB write) between timed solves"},
+           "time_to_tol_s": total_ms / args.steps / 1e3, "outer_its": st0.outer_its, "inner_its": st0.inner_its,
+           "rel_residual": max(s.rel_residual for s in stats), "gpu_launches": launches,
+           "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(bh.nbytes + xh.nbytes),
+                   "d2h_bytes_per_step": int(xh.nbytes), "ms_per_step": e2e_ms / args.steps},
+           "roofline": roofline, "clocks": clocks}
+
+    if rank == 0 and not args.no_compare:
+        comp = {}
+        for name, extra in [("fp64_sync", dict(precision="fp64", mode="sync")),
+                            ("mixed_async", dict(precision="mixed", mode="async"))]:
+            if extra["precision"] == args.precision and extra["mode"] == args.mode:
+                continue
+            x.zero_()
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, sc = grid.solve(bnd=bnd, out=x, **dict(opts, **extra, time_limit_ms=120000))
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            comp[name] = {"status": sc.status_name, "time_to_tol_s": ms / 1e3, "outer_its": sc.outer_its,
+                          "rel_residual": sc.rel_residual, "glups": sc.lups / (ms * 1e-3) / 1e9}
+        out["compare"] = comp
+        if "fp64_sync" in comp and comp["fp64_sync"]["status"] == "OK":
+            out["speedup_vs_fp64_sync"] = comp["fp64_sync"]["time_to_tol_s"] / out["time_to_tol_s"]
+    if rank == 0 and world == 1 and not args.no_cpu:
+        threads = int(os.environ.get("MS_ORACLE_THREADS", "0")) or None
+        import oracle
+        threads = threads or oracle.max_threads()
+        olups, osec = oracle_sample(cfg, 1, threads)
+        out["cpu_baseline"] = {"value": olups / osec / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+                               "sample": "1 outer sweep (residual of x^0 and x^1, 64 inner CG solves) of the full "
+                                         "workload, FP64 CPU oracle with OpenMP over blocks",
+                               "seconds": osec}
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

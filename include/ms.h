@@ -1,0 +1,172 @@
+/*
+ * ms.h -- C ABI of libms: two-stage multisplitting (outer block Jacobi,
+ * inner conjugate gradients) for the 3D Laplace 7-point stencil on one
+ * NVIDIA GB300 GPU (sm_103a).
+ *
+ * Method: Brown, Bull and Bethune, "A highly scalable approach to solving
+ * linear systems using two-stage multisplitting".
+ *   - model problem, section 2.1: Laplace's equation on a box, 7-point
+ *     stencil, Dirichlet boundary; A = 6 I - adjacency (the section 2.1
+ *     Jacobi listing averages the six neighbours with weight 1/6);
+ *   - stop rule, section 2.1: ||A x - b||_2 < tol on the global residual,
+ *     here relative to ||b||_2;
+ *   - outer stage, section 3: block Jacobi
+ *     X_i = A_ii^{-1} (B_i - sum_{j != i} A_ij X_j), right-hand side
+ *     assembled from neighbour halos only;
+ *   - inner stage, sections 2.2 and 3: a Krylov solve (CG) of each block
+ *     system, independent per block;
+ *   - synchronous or asynchronous halo exchange, sections 2.1 and 3 (the
+ *     asynchronous mode uses the latest complete neighbour data and a
+ *     possibly stale global residual, Listing 1);
+ *   - global residual from block partial sums, section 3.
+ *
+ * Conventions shared by every call:
+ *   - interior grid nx*ny*nz per right-hand side (rhs), point (i,j,k) with
+ *     0 <= i < nx stored x-fastest; a field with nrhs right-hand sides is a
+ *     C-contiguous array [nrhs][nz][ny][nx] of double;
+ *   - Dirichlet data per rhs is packed as the six faces
+ *     x-(nz*ny), x+(nz*ny), y-(nz*nx), y+(nz*nx), z-(ny*nx), z+(ny*nx), each
+ *     row-major in the order written (edges and corners are never used by a
+ *     7-point stencil and are not stored); a boundary array is
+ *     [nrhs][ms_boundary_size(nx,ny,nz)] doubles;
+ *   - unless a function says otherwise, array arguments are DEVICE pointers
+ *     on the current CUDA device, owned by the caller, never retained after
+ *     the call returns; `stream` is a cudaStream_t (NULL = legacy default
+ *     stream) on which all work of the call is ordered;
+ *   - functions return an ms_status; nothing throws or aborts across the ABI.
+ *     After a failure, ms_last_error(grid) (or ms_last_error(NULL) for a
+ *     failed ms_create_grid) describes it.  A grid handle must not be used
+ *     from two host threads at once.
+ */
+#ifndef MS_H
+#define MS_H
+
+#if defined(__GNUC__)
+#define MS_API __attribute__((visibility("default")))
+#else
+#define MS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ms_grid ms_grid;
+
+typedef enum {
+  MS_OK = 0,
+  MS_ERR_ARG = 1,            /* invalid argument; nothing was launched */
+  MS_ERR_CUDA = 2,           /* a CUDA call failed (message has the CUDA error) */
+  MS_ERR_OOM = 3,            /* device workspace could not be allocated */
+  MS_ERR_NOT_CONVERGED = 4,  /* outer_maxit sweeps done, residual still >= outer_tol */
+  MS_ERR_TIMEOUT = 5         /* time_limit_ms reached, or a bounded device wait ran out */
+} ms_status;
+
+typedef enum { MS_MODE_SYNC = 0, MS_MODE_ASYNC = 1 } ms_mode;
+
+/* FP64: inner CG vectors and arithmetic in double.
+ * MIXED: inner CG vectors and arithmetic in float; the outer residual
+ * b - A x, the global norm, the solution accumulation and the halo values
+ * stay double (two-stage iterative refinement). */
+typedef enum { MS_PREC_FP64 = 0, MS_PREC_MIXED = 1 } ms_precision;
+
+typedef struct {
+  int mode;              /* ms_mode, default MS_MODE_SYNC */
+  int precision;         /* ms_precision, default MS_PREC_MIXED */
+  double inner_rtol;     /* inner CG stop: ||r_m|| <= inner_rtol ||r_0||, default 1e-6 */
+  int inner_maxit;       /* inner CG iteration cap per block and sweep, default 50 */
+  double outer_tol;      /* stop when ||b - A x|| / ||b|| < outer_tol, default 1e-8 */
+  int outer_maxit;       /* outer sweep cap (async: per block), default 100000 */
+  double time_limit_ms;  /* host wall-clock cap for the solve, 0 = none */
+  int cluster;           /* CTAs cooperating on one block (thread-block cluster), 0 = tuned */
+  int threads;           /* threads per CTA (128, 256, 512 or 1024), 0 = tuned */
+  int slots;             /* blocks in flight at once (clusters launched), 0 = tuned */
+  int check_every;       /* sync mode: sweeps between host convergence polls, 0 = auto */
+  int use_graph;         /* sync mode: replay sweeps from a captured CUDA graph (default 1) */
+  int slow_block;        /* async resilience test: this block id sleeps slow_ns per visit; -1 = none */
+  int slow_ns;           /*   bounded __nanosleep budget per visit of slow_block */
+  double* res_hist;      /* HOST, optional: [nrhs][outer_maxit+1] relative residual per sweep
+                            (sync mode; entries after each rhs stops are left untouched) */
+  int profile;           /* sync mode: time every sweep kernel with CUDA events (stats.sweep_ms) */
+} ms_opts;
+
+typedef struct {
+  int status;            /* ms_status of the solve */
+  int outer_its;         /* sync: max over rhs of sweeps K with x = x^K; async: max sweeps of any block */
+  long long inner_its;   /* total inner CG iterations over all blocks, rhs and sweeps */
+  long long lups;        /* stencil lattice updates: inner iterations x block points + residual points */
+  double rel_residual;   /* max over rhs of the true final ||b - A x|| / ||b|| (absolute if ||b|| = 0) */
+  double time_ms;        /* device time of the solve on `stream` (CUDA events) */
+  int launches;          /* solver kernel launches (sweep, check and residual kernels) */
+  int cluster, threads, slots; /* launch shape used */
+  int* per_rhs_outer_its;      /* HOST, optional [nrhs]: filled if non-NULL */
+  double* per_rhs_rel;         /* HOST, optional [nrhs]: filled if non-NULL */
+  double sweep_ms;             /* with opts.profile: summed device time of the sweep kernels */
+  int sweep_launches;          /* with opts.profile: sweep kernels timed */
+} ms_stats;
+
+/* Number of doubles in one rhs's packed boundary array. */
+MS_API long long ms_boundary_size(int nx, int ny, int nz);
+
+/* Fill *opts with the defaults listed above. */
+MS_API void ms_default_opts(ms_opts* opts);
+
+/* Create a grid of nx*ny*nz interior points with nrhs right-hand sides
+ * (section 2.1 model problem).  *out receives a handle owned by the caller
+ * (free with ms_destroy).  Sizes must be >= 1.  Partitioned as one block
+ * until ms_partition is called. */
+MS_API int ms_create_grid(int nx, int ny, int nz, int nrhs, ms_grid** out);
+
+/* Block layout (section 3: the matrix split into blocks by a domain
+ * decomposition): px*py*pz blocks with per-axis cut arrays cx[0..px],
+ * cy[0..py], cz[0..pz] (HOST int arrays, strictly increasing from 0 to n;
+ * copied).  A NULL cut array means an equal split with the remainder given
+ * to the leading blocks.  Block id = bx + px*(by + py*bz).  Fails with
+ * MS_ERR_ARG if an edge is < 1. */
+MS_API int ms_partition(ms_grid* grid, int px, int py, int pz, const int* cx, const int* cy, const int* cz);
+
+/* Copy the current cut arrays to HOST arrays of length px+1, py+1, pz+1. */
+MS_API int ms_get_cuts(ms_grid* grid, int* cx, int* cy, int* cz);
+
+/* Solve A x = bhat for every rhs, bhat = f + lift(bnd) (section 2.1 problem,
+ * section 3 method, Listing 1 loop).
+ *   f:   [nrhs][nz][ny][nx] interior source, or NULL for zero;
+ *   bnd: [nrhs][ms_boundary_size] Dirichlet faces, or NULL for zero;
+ *   x:   [nrhs][nz][ny][nx], in: initial guess x^0, out: solution;
+ *   opts: HOST, NULL = defaults; stats: HOST, may be NULL.
+ * Each rhs stops independently at the first x^K with relative residual
+ * < outer_tol (sync mode; tested on x^k before sweep k+1).  Blocks until the
+ * solve is finished (the result is ready on `stream`'s timeline when it
+ * returns).  Returns MS_ERR_NOT_CONVERGED if any rhs hit outer_maxit, with x
+ * holding the last iterate. */
+MS_API int ms_solve(ms_grid* grid, const double* f, const double* bnd, double* x, const ms_opts* opts, ms_stats* stats,
+             void* stream);
+
+/* ms_solve with HOST arrays (pageable or pinned): copies f, bnd and x to
+ * device workspace, solves, copies x back, all on `stream`. */
+MS_API int ms_solve_host(ms_grid* grid, const double* f_host, const double* bnd_host, double* x_host,
+                  const ms_opts* opts, ms_stats* stats, void* stream);
+
+/* True relative residual ||bhat - A x||_2 / ||bhat||_2 per rhs (section 2.1
+ * stop-rule norm), computed from scratch in FP64.  rel_out: HOST [nrhs];
+ * where ||bhat|| = 0 the absolute norm is returned.  Synchronises `stream`. */
+MS_API int ms_residual(ms_grid* grid, const double* f, const double* bnd, const double* x, double* rel_out, void* stream);
+
+/* Adjoint helper: since bhat = f + lift(g), d bhat_q / d g_p = 1 for the
+ * interior point q next to boundary point p.  Writes grad_bnd[s][p] =
+ * lam[s][q(p)] for every packed boundary point p ([nrhs][ms_boundary_size],
+ * device).  lam is [nrhs][nz][ny][nx] (device). */
+MS_API int ms_face_gather(ms_grid* grid, const double* lam, double* grad_bnd, void* stream);
+
+/* Free the handle and its device workspace.  Synchronises the device work
+ * the handle issued.  NULL is accepted. */
+MS_API int ms_destroy(ms_grid* grid);
+
+/* Message for the last failure on this handle (or of ms_create_grid when
+ * grid is NULL).  Valid until the next call on the handle. */
+MS_API const char* ms_last_error(ms_grid* grid);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,282 @@
+"""GB300-native two-stage multisplitting for the 3D Laplace 7-point stencil.
+
+Outer block Jacobi (synchronous or asynchronous) with an inner CG per block,
+after Brown, Bull and Bethune, "A highly scalable approach to solving linear
+systems using two-stage multisplitting" (sections 2.1, 2.2, 3; Listing 1).
+
+This package is a thin layer over the CUDA library libms.so and its C ABI
+(include/ms.h): PyTorch supplies device memory and the current stream, every
+step of the solve runs in the library's sm_103a kernels.  There is no CPU
+fallback; if the library is missing, importing the solver raises.
+
+    grid = Grid(nx, ny, nz, nrhs)
+    grid.partition(px, py, pz)                 # or explicit cut arrays
+    x, stats = grid.solve(f=None, bnd=g, precision="mixed", mode="sync")
+    u = MsSolve.apply(f, g, grid, opts)        # differentiable in f and g
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib
+
+__all__ = ["Grid", "SolveStats", "MsSolve", "boundary_size", "MsError"]
+
+MsError = _lib.MsError
+
+
+def boundary_size(nx: int, ny: int, nz: int) -> int:
+    return 2 * nz * ny + 2 * nz * nx + 2 * ny * nx
+
+
+@dataclass
+class SolveStats:
+    status: int
+    outer_its: int
+    inner_its: int
+    lups: int
+    rel_residual: float
+    time_ms: float
+    launches: int
+    cluster: int
+    threads: int
+    slots: int
+    per_rhs_outer_its: list
+    per_rhs_rel: list
+    sweep_ms: float = 0.0
+    sweep_launches: int = 0
+    history: np.ndarray | None = None
+
+    @property
+    def status_name(self):
+        return _lib.STATUS_NAMES.get(self.status, str(self.status))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream_handle(device):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _make_opts(lib, mode="sync", precision="mixed", inner_rtol=1e-6, inner_maxit=50, outer_tol=1e-8,
+               outer_maxit=100000, time_limit_ms=0.0, cluster=0, threads=0, slots=0, check_every=0, use_graph=True,
+               slow_block=-1, slow_ns=0, profile=False):
+    o = _lib.Opts()
+    lib.ms_default_opts(ctypes.byref(o))
+    o.mode = _lib.MODE[mode] if isinstance(mode, str) else int(mode)
+    o.precision = _lib.PRECISION[precision] if isinstance(precision, str) else int(precision)
+    o.inner_rtol = float(inner_rtol)
+    o.inner_maxit = int(inner_maxit)
+    o.outer_tol = float(outer_tol)
+    o.outer_maxit = int(outer_maxit)
+    o.time_limit_ms = float(time_limit_ms)
+    o.cluster = int(cluster)
+    o.threads = int(threads)
+    o.slots = int(slots)
+    o.check_every = int(check_every)
+    o.use_graph = 1 if use_graph else 0
+    o.slow_block = int(slow_block)
+    o.slow_ns = int(slow_ns)
+    o.profile = 1 if profile else 0
+    return o
+
+
+class Grid:
+    """A grid handle (ms_create_grid) with its block partition and workspace."""
+
+    def __init__(self, nx: int, ny: int, nz: int, nrhs: int = 1, device=None):
+        self._lib = _lib.load()
+        self.nx, self.ny, self.nz, self.nrhs = int(nx), int(ny), int(nz), int(nrhs)
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = self._lib.ms_create_grid(self.nx, self.ny, self.nz, self.nrhs, ctypes.byref(h))
+        if rc != _lib.MS_OK:
+            raise _lib.MsError(rc, self._lib.ms_last_error(None).decode())
+        self._h = h
+        self.px = self.py = self.pz = 1
+
+    # ------------------------------------------------------------------ housekeeping
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.ms_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc not in (_lib.MS_OK,):
+            raise _lib.MsError(rc, self._lib.ms_last_error(self._h).decode())
+
+    @property
+    def shape(self):
+        return (self.nrhs, self.nz, self.ny, self.nx)
+
+    @property
+    def npts(self):
+        return self.nx * self.ny * self.nz
+
+    @property
+    def nbnd(self):
+        return boundary_size(self.nx, self.ny, self.nz)
+
+    def partition(self, px, py, pz, cx=None, cy=None, cz=None):
+        arr = []
+        for c in (cx, cy, cz):
+            arr.append(None if c is None else (ctypes.c_int * len(c))(*[int(v) for v in c]))
+        self._check(self._lib.ms_partition(self._h, int(px), int(py), int(pz), *arr))
+        self.px, self.py, self.pz = int(px), int(py), int(pz)
+        return self
+
+    def cuts(self):
+        cx = (ctypes.c_int * (self.px + 1))()
+        cy = (ctypes.c_int * (self.py + 1))()
+        cz = (ctypes.c_int * (self.pz + 1))()
+        self._check(self._lib.ms_get_cuts(self._h, cx, cy, cz))
+        return list(cx), list(cy), list(cz)
+
+    def _field(self, t, name, shape, allow_none=True):
+        if t is None:
+            if allow_none:
+                return None
+            raise ValueError(f"{name} is required")
+        if not isinstance(t, torch.Tensor):
+            t = torch.as_tensor(np.asarray(t, dtype=np.float64))
+        if t.dtype != torch.float64:
+            raise TypeError(f"{name} must be float64")
+        if t.device != self.device:
+            t = t.to(self.device)
+        t = t.contiguous()
+        if t.numel() != int(np.prod(shape)):
+            raise ValueError(f"{name} must have {int(np.prod(shape))} elements, got {t.numel()}")
+        return t.view(shape)
+
+    # ------------------------------------------------------------------ solver calls
+    def solve(self, f=None, bnd=None, x0=None, out=None, history=False, **opts):
+        """Solve A x = f + lift(bnd) for every rhs; returns (x, SolveStats).
+
+        f: (nrhs, nz, ny, nx) or None; bnd: (nrhs, nbnd) or None;
+        x0: initial guess (default zero); out: optional result tensor (may be x0).
+        opts: mode ('sync'|'async'), precision ('mixed'|'fp64'), inner_rtol,
+        inner_maxit, outer_tol, outer_maxit, time_limit_ms, cluster, threads,
+        slots, check_every, use_graph, slow_block, slow_ns, profile.
+        """
+        f = self._field(f, "f", self.shape)
+        bnd = self._field(bnd, "bnd", (self.nrhs, self.nbnd))
+        if out is None:
+            out = torch.zeros(self.shape, dtype=torch.float64, device=self.device)
+            if x0 is not None:
+                out.copy_(self._field(x0, "x0", self.shape, allow_none=False))
+        else:
+            if out.dtype != torch.float64 or not out.is_contiguous() or out.device != self.device:
+                raise ValueError("out must be a contiguous float64 tensor on the grid's device")
+            if x0 is not None and x0.data_ptr() != out.data_ptr():
+                out.copy_(self._field(x0, "x0", self.shape, allow_none=False))
+        o = _make_opts(self._lib, **opts)
+        hist = None
+        if history:
+            hist = np.zeros((self.nrhs, o.outer_maxit + 1))
+            o.res_hist = hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        st = _lib.Stats()
+        per_its = (ctypes.c_int * self.nrhs)()
+        per_rel = (ctypes.c_double * self.nrhs)()
+        st.per_rhs_outer_its = per_its
+        st.per_rhs_rel = per_rel
+        with torch.cuda.device(self.device):
+            rc = self._lib.ms_solve(self._h, _ptr(f), _ptr(bnd), _ptr(out), ctypes.byref(o), ctypes.byref(st),
+                                    _stream_handle(self.device))
+        if rc not in (_lib.MS_OK, _lib.MS_ERR_NOT_CONVERGED, _lib.MS_ERR_TIMEOUT):
+            self._check(rc)
+        stats = SolveStats(rc, st.outer_its, st.inner_its, st.lups, st.rel_residual, st.time_ms, st.launches,
+                           st.cluster, st.threads, st.slots, list(per_its), list(per_rel), st.sweep_ms,
+                           st.sweep_launches)
+        if hist is not None:
+            stats.history = hist
+        return out, stats
+
+    def solve_host(self, f=None, bnd=None, x=None, **opts):
+        """ms_solve_host: numpy (host) arrays in, solution written into x (host)."""
+        def host(a, shape):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            if a.size != int(np.prod(shape)):
+                raise ValueError("wrong size")
+            return a
+        f = host(f, self.shape)
+        bnd = host(bnd, (self.nrhs, self.nbnd))
+        if x is None:
+            x = np.zeros(self.shape)
+        if not (isinstance(x, np.ndarray) and x.dtype == np.float64 and x.flags.c_contiguous):
+            raise ValueError("x must be a C-contiguous float64 numpy array")
+        o = _make_opts(self._lib, **opts)
+        st = _lib.Stats()
+        p = lambda a: None if a is None else ctypes.c_void_p(a.ctypes.data)  # noqa: E731
+        with torch.cuda.device(self.device):
+            rc = self._lib.ms_solve_host(self._h, p(f), p(bnd), p(x), ctypes.byref(o), ctypes.byref(st),
+                                         _stream_handle(self.device))
+        if rc not in (_lib.MS_OK, _lib.MS_ERR_NOT_CONVERGED, _lib.MS_ERR_TIMEOUT):
+            self._check(rc)
+        return x, SolveStats(rc, st.outer_its, st.inner_its, st.lups, st.rel_residual, st.time_ms, st.launches,
+                             st.cluster, st.threads, st.slots, [], [])
+
+    def residual(self, x, f=None, bnd=None):
+        """True relative residual per rhs (absolute where ||bhat|| = 0), computed on the GPU."""
+        f = self._field(f, "f", self.shape)
+        bnd = self._field(bnd, "bnd", (self.nrhs, self.nbnd))
+        x = self._field(x, "x", self.shape, allow_none=False)
+        out = (ctypes.c_double * self.nrhs)()
+        with torch.cuda.device(self.device):
+            self._check(self._lib.ms_residual(self._h, _ptr(f), _ptr(bnd), _ptr(x), out,
+                                              _stream_handle(self.device)))
+        return np.array(list(out))
+
+    def face_gather(self, lam):
+        """grad_bnd[s][p] = lam[s][q(p)] (the adjoint of the boundary lift)."""
+        lam = self._field(lam, "lam", self.shape, allow_none=False)
+        out = torch.empty((self.nrhs, self.nbnd), dtype=torch.float64, device=self.device)
+        with torch.cuda.device(self.device):
+            self._check(self._lib.ms_face_gather(self._h, _ptr(lam), _ptr(out), _stream_handle(self.device)))
+        return out
+
+
+class MsSolve(torch.autograd.Function):
+    """u = A^{-1}(f + lift(bnd)) with a hand-written adjoint.
+
+    A is symmetric (the 7-point Laplacian), so the backward pass solves
+    A lam = dL/du with the same block solver and returns dL/df = lam and
+    dL/dbnd = lam at the interior point next to each boundary point.  The
+    forward solution is saved (checkpointed) for reuse as the caller needs it.
+    """
+
+    @staticmethod
+    def forward(ctx, f, bnd, grid: Grid, opts: dict):
+        opts = dict(opts or {})
+        u, st = grid.solve(f=f, bnd=bnd, **opts)
+        if st.status not in (_lib.MS_OK,):
+            raise _lib.MsError(st.status, "forward solve did not converge")
+        ctx.grid = grid
+        ctx.opts = opts
+        ctx.save_for_backward(u)
+        ctx.forward_stats = st
+        return u
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        grid = ctx.grid
+        lam, st = grid.solve(f=grad_u.contiguous(), bnd=None, **ctx.opts)
+        if st.status not in (_lib.MS_OK,):
+            raise _lib.MsError(st.status, "adjoint solve did not converge")
+        grad_f = lam if ctx.needs_input_grad[0] else None
+        grad_b = grid.face_gather(lam) if ctx.needs_input_grad[1] else None
+        return grad_f, grad_b, None, None

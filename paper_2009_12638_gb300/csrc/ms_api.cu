@@ -1,0 +1,792 @@
+// ms_api.cu -- host side of libms: the C ABI declared in include/ms.h.
+//
+// Owns the grid handle, the block partition, the device workspace and the
+// solve loop.  All device work is ordered on the caller's stream; the library
+// allocates its own workspace once per handle and grows it on demand.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ms.h"
+#include "ms_internal.h"
+#include "ms_tune.h"
+
+using namespace ms;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  // grow (never shrink); contents are not preserved
+  cudaError_t reserve(size_t want) {
+    if (want <= bytes) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return e;
+    }
+    bytes = want;
+    return cudaSuccess;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <typename T>
+  T* as() const {
+    return reinterpret_cast<T*>(p);
+  }
+};
+
+// small per-solve device state, one allocation
+struct Ctl {
+  unsigned int counter;
+  int all_done;
+  int k_dev;
+  int err;
+  int stop;
+  int pad[3];
+};
+
+}  // namespace
+
+struct ms_grid {
+  int nx, ny, nz, nrhs;
+  int px = 1, py = 1, pz = 1;
+  std::vector<int> cx, cy, cz;
+  std::string err;
+  int device = 0;
+  // workspace
+  DevBuf xalt;     // second x buffer [nrhs][npts]
+  DevBuf scratch;  // per-slot CG vectors
+  DevBuf tasks;    // Task[ntasks]
+  DevBuf partial;  // double[ntasks]
+  DevBuf ctl;      // Ctl + per-rhs arrays
+  DevBuf hist;     // [nrhs][outer_maxit+1]
+  DevBuf rpart;    // residual partials
+  DevBuf host_io;  // device copies for ms_solve_host: f, bnd, x
+  DevBuf async_ws; // face buffers, halos, seq counters (async mode)
+  Tuner tuner;
+  long long npts() const { return (long long)nx * ny * nz; }
+  long long nbnd() const { return ms_boundary_size(nx, ny, nz); }
+  Geo geo() const { return Geo{nx, ny, nz, nrhs, npts(), nbnd()}; }
+};
+
+static int fail(ms_grid* g, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (g) g->err = buf;
+  else g_create_error = buf;
+  return code;
+}
+
+#define MS_CUDA(g, expr)                                                                        \
+  do {                                                                                          \
+    cudaError_t e_ = (expr);                                                                    \
+    if (e_ != cudaSuccess)                                                                      \
+      return fail((g), e_ == cudaErrorMemoryAllocation ? MS_ERR_OOM : MS_ERR_CUDA, "%s: %s (%s)", \
+                  #expr, cudaGetErrorName(e_), cudaGetErrorString(e_));                         \
+  } while (0)
+
+extern "C" long long ms_boundary_size(int nx, int ny, int nz) {
+  return 2LL * nz * ny + 2LL * nz * nx + 2LL * ny * nx;
+}
+
+extern "C" void ms_default_opts(ms_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->mode = MS_MODE_SYNC;
+  o->precision = MS_PREC_MIXED;
+  o->inner_rtol = 1e-6;
+  o->inner_maxit = 50;
+  o->outer_tol = 1e-8;
+  o->outer_maxit = 100000;
+  o->time_limit_ms = 0.0;
+  o->cluster = 0;
+  o->threads = 0;
+  o->slots = 0;
+  o->check_every = 0;
+  o->use_graph = 1;
+  o->slow_block = -1;
+  o->slow_ns = 0;
+  o->res_hist = nullptr;
+  o->profile = 0;
+}
+
+static std::vector<int> equal_cuts(int n, int p) {
+  std::vector<int> c(p + 1, 0);
+  int q = n / p, rem = n % p;
+  for (int a = 0; a < p; ++a) c[a + 1] = c[a] + q + (a < rem ? 1 : 0);
+  return c;
+}
+
+extern "C" int ms_create_grid(int nx, int ny, int nz, int nrhs, ms_grid** out) {
+  if (!out) return fail(nullptr, MS_ERR_ARG, "ms_create_grid: out is NULL");
+  *out = nullptr;
+  if (nx < 1 || ny < 1 || nz < 1 || nrhs < 1)
+    return fail(nullptr, MS_ERR_ARG, "ms_create_grid: sizes must be >= 1 (got %d %d %d nrhs %d)", nx, ny, nz, nrhs);
+  const double total = (double)nx * ny * nz * nrhs;
+  if (total > 9.0e15) return fail(nullptr, MS_ERR_ARG, "ms_create_grid: grid too large");
+  if ((long long)nx * ny > 0x7fffffffLL || (long long)nx * nz > 0x7fffffffLL || (long long)ny * nz > 0x7fffffffLL)
+    return fail(nullptr, MS_ERR_ARG, "ms_create_grid: a face exceeds 2^31 points");
+  ms_grid* g = new ms_grid();
+  g->nx = nx;
+  g->ny = ny;
+  g->nz = nz;
+  g->nrhs = nrhs;
+  g->cx = {0, nx};
+  g->cy = {0, ny};
+  g->cz = {0, nz};
+  cudaGetDevice(&g->device);
+  *out = g;
+  return MS_OK;
+}
+
+static bool valid_cuts(const int* c, int p, int n) {
+  if (c[0] != 0 || c[p] != n) return false;
+  for (int a = 0; a < p; ++a)
+    if (c[a + 1] <= c[a]) return false;
+  return true;
+}
+
+extern "C" int ms_partition(ms_grid* g, int px, int py, int pz, const int* cx, const int* cy, const int* cz) {
+  if (!g) return MS_ERR_ARG;
+  if (px < 1 || py < 1 || pz < 1) return fail(g, MS_ERR_ARG, "ms_partition: block counts must be >= 1");
+  if (px > g->nx || py > g->ny || pz > g->nz)
+    return fail(g, MS_ERR_ARG, "ms_partition: more blocks than points along an axis (edge < 1)");
+  std::vector<int> ax = cx ? std::vector<int>(cx, cx + px + 1) : equal_cuts(g->nx, px);
+  std::vector<int> ay = cy ? std::vector<int>(cy, cy + py + 1) : equal_cuts(g->ny, py);
+  std::vector<int> az = cz ? std::vector<int>(cz, cz + pz + 1) : equal_cuts(g->nz, pz);
+  if (!valid_cuts(ax.data(), px, g->nx) || !valid_cuts(ay.data(), py, g->ny) || !valid_cuts(az.data(), pz, g->nz))
+    return fail(g, MS_ERR_ARG, "ms_partition: cuts must rise strictly from 0 to n (every edge >= 1)");
+  const long long nb = (long long)px * py * pz;
+  if (nb * g->nrhs > 0x3fffffffLL) return fail(g, MS_ERR_ARG, "ms_partition: too many blocks");
+  g->px = px;
+  g->py = py;
+  g->pz = pz;
+  g->cx = ax;
+  g->cy = ay;
+  g->cz = az;
+  return MS_OK;
+}
+
+extern "C" int ms_get_cuts(ms_grid* g, int* cx, int* cy, int* cz) {
+  if (!g || !cx || !cy || !cz) return g ? fail(g, MS_ERR_ARG, "ms_get_cuts: NULL output") : MS_ERR_ARG;
+  std::copy(g->cx.begin(), g->cx.end(), cx);
+  std::copy(g->cy.begin(), g->cy.end(), cy);
+  std::copy(g->cz.begin(), g->cz.end(), cz);
+  return MS_OK;
+}
+
+// Tasks: every (block, rhs), largest blocks first (longest-processing-time
+// order for the dynamic queue), ties in (rhs, block id) order.
+static std::vector<Task> build_tasks(const ms_grid* g, long long* max_pts) {
+  std::vector<Task> ts;
+  long long mx = 0;
+  for (int s = 0; s < g->nrhs; ++s)
+    for (int bk = 0; bk < g->pz; ++bk)
+      for (int bj = 0; bj < g->py; ++bj)
+        for (int bi = 0; bi < g->px; ++bi) {
+          Task t;
+          t.ox = g->cx[bi];
+          t.oy = g->cy[bj];
+          t.oz = g->cz[bk];
+          t.bx = g->cx[bi + 1] - t.ox;
+          t.by = g->cy[bj + 1] - t.oy;
+          t.bz = g->cz[bk + 1] - t.oz;
+          t.rhs = s;
+          t.block = bi + g->px * (bj + g->py * bk);
+          mx = std::max(mx, (long long)t.bx * t.by * t.bz);
+          ts.push_back(t);
+        }
+  std::stable_sort(ts.begin(), ts.end(), [](const Task& a, const Task& b) {
+    return (long long)a.bx * a.by * a.bz > (long long)b.bx * b.by * b.bz;
+  });
+  *max_pts = mx;
+  return ts;
+}
+
+static int check_opts(ms_grid* g, const ms_opts& o) {
+  if (o.mode != MS_MODE_SYNC && o.mode != MS_MODE_ASYNC) return fail(g, MS_ERR_ARG, "opts.mode must be SYNC or ASYNC");
+  if (o.precision != MS_PREC_FP64 && o.precision != MS_PREC_MIXED)
+    return fail(g, MS_ERR_ARG, "opts.precision must be FP64 or MIXED");
+  if (!(o.inner_rtol >= 0.0) || o.inner_maxit < 0 || !(o.outer_tol >= 0.0) || o.outer_maxit < 0)
+    return fail(g, MS_ERR_ARG, "opts: tolerances must be >= 0 and iteration caps >= 0");
+  if (o.cluster < 0 || o.cluster > kMaxCluster) return fail(g, MS_ERR_ARG, "opts.cluster must be 0..16");
+  if (o.threads != 0 && o.threads != 256 && o.threads != 512 && o.threads != 1024)
+    return fail(g, MS_ERR_ARG, "opts.threads must be 0, 256, 512 or 1024");
+  if (o.slots < 0 || o.check_every < 0) return fail(g, MS_ERR_ARG, "opts.slots and opts.check_every must be >= 0");
+  if (o.time_limit_ms < 0.0) return fail(g, MS_ERR_ARG, "opts.time_limit_ms must be >= 0");
+  return MS_OK;
+}
+
+// Per-rhs bookkeeping arrays live after Ctl in the ctl buffer.
+struct CtlLayout {
+  size_t off_state, off_kfinal, off_inner, off_invb, off_norm, bytes;
+};
+static CtlLayout ctl_layout(int nrhs) {
+  CtlLayout L;
+  size_t o = 256;
+  L.off_state = o;
+  o += ((size_t)nrhs * sizeof(int) + 255) / 256 * 256;
+  L.off_kfinal = o;
+  o += ((size_t)nrhs * sizeof(int) + 255) / 256 * 256;
+  L.off_inner = o;
+  o += ((size_t)nrhs * 2 * sizeof(unsigned long long) + 255) / 256 * 256;
+  L.off_invb = o;
+  o += ((size_t)nrhs * sizeof(double) + 255) / 256 * 256;
+  L.off_norm = o;
+  o += ((size_t)nrhs * 2 * sizeof(double) + 255) / 256 * 256;
+  L.bytes = o;
+  return L;
+}
+
+static int resid_blocks(long long npts) {
+  long long b = (npts + 255) / 256;
+  return (int)std::max(1LL, std::min(b, 152LL * 8));
+}
+
+// true residual norms of x: out[2s] = ||bhat - A x||^2, out[2s+1] = ||bhat||^2 (device), inv_bnorm optional
+static int run_resid(ms_grid* g, const double* f, const double* bnd, const double* x, double* out_dev,
+                     double* invb_dev, cudaStream_t st) {
+  const int nblk = resid_blocks(g->npts());
+  MS_CUDA(g, g->rpart.reserve((size_t)g->nrhs * nblk * 2 * sizeof(double)));
+  ResidArgs ra{g->geo(), f, bnd, x, g->rpart.as<double>(), nblk};
+  MS_CUDA(g, launch_resid(ra, out_dev, invb_dev, st));
+  return MS_OK;
+}
+
+static int solve_device(ms_grid* g, const double* f, const double* bnd, double* x, const ms_opts& o, ms_stats* st,
+                        cudaStream_t stream);
+
+extern "C" int ms_solve(ms_grid* g, const double* f, const double* bnd, double* x, const ms_opts* opts,
+                        ms_stats* stats, void* stream) {
+  if (!g) return MS_ERR_ARG;
+  if (!x) return fail(g, MS_ERR_ARG, "ms_solve: x is NULL");
+  ms_opts o;
+  if (opts) o = *opts;
+  else ms_default_opts(&o);
+  int rc = check_opts(g, o);
+  if (rc != MS_OK) return rc;
+  return solve_device(g, f, bnd, x, o, stats, (cudaStream_t)stream);
+}
+
+extern "C" int ms_solve_host(ms_grid* g, const double* f_host, const double* bnd_host, double* x_host,
+                             const ms_opts* opts, ms_stats* stats, void* stream) {
+  if (!g) return MS_ERR_ARG;
+  if (!x_host) return fail(g, MS_ERR_ARG, "ms_solve_host: x is NULL");
+  ms_opts o;
+  if (opts) o = *opts;
+  else ms_default_opts(&o);
+  int rc = check_opts(g, o);
+  if (rc != MS_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t fx = (size_t)g->nrhs * g->npts() * sizeof(double);
+  const size_t fb = (size_t)g->nrhs * g->nbnd() * sizeof(double);
+  const size_t offb = (fx + 255) / 256 * 256, offx = offb + (fb + 255) / 256 * 256;
+  MS_CUDA(g, g->host_io.reserve(offx + fx));
+  char* base = g->host_io.as<char>();
+  double* fd = f_host ? reinterpret_cast<double*>(base) : nullptr;
+  double* bd = bnd_host ? reinterpret_cast<double*>(base + offb) : nullptr;
+  double* xd = reinterpret_cast<double*>(base + offx);
+  if (fd) MS_CUDA(g, cudaMemcpyAsync(fd, f_host, fx, cudaMemcpyHostToDevice, s));
+  if (bd) MS_CUDA(g, cudaMemcpyAsync(bd, bnd_host, fb, cudaMemcpyHostToDevice, s));
+  MS_CUDA(g, cudaMemcpyAsync(xd, x_host, fx, cudaMemcpyHostToDevice, s));
+  rc = solve_device(g, fd, bd, xd, o, stats, s);
+  if (rc != MS_OK && rc != MS_ERR_NOT_CONVERGED) return rc;
+  MS_CUDA(g, cudaMemcpyAsync(x_host, xd, fx, cudaMemcpyDeviceToHost, s));
+  MS_CUDA(g, cudaStreamSynchronize(s));
+  return rc;
+}
+
+extern "C" int ms_residual(ms_grid* g, const double* f, const double* bnd, const double* x, double* rel_out,
+                           void* stream) {
+  if (!g) return MS_ERR_ARG;
+  if (!x || !rel_out) return fail(g, MS_ERR_ARG, "ms_residual: x and rel_out must be non-NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  CtlLayout L = ctl_layout(g->nrhs);
+  MS_CUDA(g, g->ctl.reserve(L.bytes));
+  double* norms = reinterpret_cast<double*>(g->ctl.as<char>() + L.off_norm);
+  int rc = run_resid(g, f, bnd, x, norms, nullptr, s);
+  if (rc != MS_OK) return rc;
+  std::vector<double> h(2 * (size_t)g->nrhs);
+  MS_CUDA(g, cudaMemcpyAsync(h.data(), norms, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  MS_CUDA(g, cudaStreamSynchronize(s));
+  for (int r = 0; r < g->nrhs; ++r)
+    rel_out[r] = h[2 * r + 1] > 0.0 ? std::sqrt(h[2 * r]) / std::sqrt(h[2 * r + 1]) : std::sqrt(h[2 * r]);
+  return MS_OK;
+}
+
+extern "C" int ms_face_gather(ms_grid* g, const double* lam, double* grad_bnd, void* stream) {
+  if (!g) return MS_ERR_ARG;
+  if (!lam || !grad_bnd) return fail(g, MS_ERR_ARG, "ms_face_gather: NULL argument");
+  MS_CUDA(g, launch_face_gather(g->geo(), lam, grad_bnd, (cudaStream_t)stream));
+  return MS_OK;
+}
+
+extern "C" int ms_destroy(ms_grid* g) {
+  if (!g) return MS_OK;
+  cudaDeviceSynchronize();
+  g->xalt.release();
+  g->scratch.release();
+  g->tasks.release();
+  g->partial.release();
+  g->ctl.release();
+  g->hist.release();
+  g->rpart.release();
+  g->host_io.release();
+  g->async_ws.release();
+  g->tuner.release();
+  delete g;
+  return MS_OK;
+}
+
+extern "C" const char* ms_last_error(ms_grid* g) {
+  if (!g) return g_create_error.c_str();
+  return g->err.c_str();
+}
+
+// ------------------------------------------------------------------ solve
+int solve_async(ms_grid* g, const double* f, const double* bnd, double* x, const ms_opts& o, ms_stats* st,
+                cudaStream_t stream, const LaunchShape& shape, const std::vector<Task>& tasks, long long maxpts,
+                double* invb_dev, int* rc_out);
+
+static int solve_device(ms_grid* g, const double* f, const double* bnd, double* x, const ms_opts& o, ms_stats* st,
+                        cudaStream_t stream) {
+  const int prec = o.precision == MS_PREC_MIXED ? 1 : 0;
+  const size_t esz = prec ? sizeof(float) : sizeof(double);
+  long long maxpts = 0;
+  std::vector<Task> tasks = build_tasks(g, &maxpts);
+  const int ntasks = (int)tasks.size();
+  const long long npts = g->npts();
+  const size_t xbytes = (size_t)g->nrhs * npts * sizeof(double);
+
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  MS_CUDA(g, cudaEventCreate(&ev0));
+  MS_CUDA(g, cudaEventCreate(&ev1));
+  struct EvGuard {
+    cudaEvent_t a, b;
+    ~EvGuard() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } evg{ev0, ev1};
+
+  // launch shape
+  LaunchShape shape;
+  int rc = choose_shape(g->tuner, prec, o.mode, tasks, maxpts, o.cluster, o.threads, o.slots, &shape);
+  if (rc != 0) return fail(g, MS_ERR_CUDA, "ms_solve: no launchable shape (%s)", cudaGetErrorString((cudaError_t)rc));
+
+  // workspace
+  const long long vec_stride = (maxpts + 31) / 32 * 32;
+  CtlLayout L = ctl_layout(g->nrhs);
+  MS_CUDA(g, g->scratch.reserve((size_t)shape.slots * 4 * vec_stride * esz));
+  MS_CUDA(g, g->tasks.reserve(tasks.size() * sizeof(Task)));
+  MS_CUDA(g, g->partial.reserve((size_t)ntasks * sizeof(double)));
+  MS_CUDA(g, g->ctl.reserve(L.bytes));
+  char* ctlb = g->ctl.as<char>();
+  Ctl* ctl = reinterpret_cast<Ctl*>(ctlb);
+  int* rhs_state = reinterpret_cast<int*>(ctlb + L.off_state);
+  int* k_final = reinterpret_cast<int*>(ctlb + L.off_kfinal);
+  unsigned long long* inner = reinterpret_cast<unsigned long long*>(ctlb + L.off_inner);
+  double* invb = reinterpret_cast<double*>(ctlb + L.off_invb);
+  double* norms = reinterpret_cast<double*>(ctlb + L.off_norm);
+
+  MS_CUDA(g, cudaEventRecord(ev0, stream));
+  MS_CUDA(g, cudaMemcpyAsync(g->tasks.p, tasks.data(), tasks.size() * sizeof(Task), cudaMemcpyHostToDevice, stream));
+  MS_CUDA(g, cudaMemsetAsync(ctlb, 0, L.bytes, stream));
+  // ||bhat|| per rhs (and the residual of x^0, unused here)
+  rc = run_resid(g, f, bnd, x, norms, invb, stream);
+  if (rc != MS_OK) return rc;
+  int launches = 2;
+
+  int status = MS_OK;
+  int outer_max = 0;
+  std::vector<int> h_kfinal(g->nrhs, 0), h_state(g->nrhs, 0);
+  if (o.mode == MS_MODE_ASYNC) {
+    int arc = MS_OK;
+    rc = solve_async(g, f, bnd, x, o, st, stream, shape, tasks, maxpts, invb, &arc);
+    if (rc != MS_OK) return rc;
+    status = arc;
+    launches += st ? st->launches : 0;
+    if (st) st->launches = 0;
+  } else {
+    MS_CUDA(g, g->xalt.reserve(xbytes));
+    double* hist_dev = nullptr;
+    if (o.res_hist) {
+      MS_CUDA(g, g->hist.reserve((size_t)g->nrhs * (o.outer_maxit + 1) * sizeof(double)));
+      hist_dev = g->hist.as<double>();
+    }
+    SweepArgs sa;
+    sa.g = g->geo();
+    sa.f = f;
+    sa.bnd = bnd;
+    sa.xbuf0 = x;
+    sa.xbuf1 = g->xalt.as<double>();
+    sa.tasks = g->tasks.as<Task>();
+    sa.ntasks = ntasks;
+    sa.counter = &ctl->counter;
+    sa.rhs_state = rhs_state;
+    sa.all_done = &ctl->all_done;
+    sa.partial = g->partial.as<double>();
+    sa.scratch = g->scratch.p;
+    sa.vec_stride = vec_stride;
+    sa.inner_rtol = o.inner_rtol;
+    sa.inner_maxit = o.inner_maxit;
+    sa.outer_maxit = o.outer_maxit;
+    sa.k_dev = &ctl->k_dev;
+    sa.inner_count = inner;
+    sa.err = &ctl->err;
+    CheckArgs ca;
+    ca.nrhs = g->nrhs;
+    ca.ntasks = ntasks;
+    ca.tasks = sa.tasks;
+    ca.partial = sa.partial;
+    ca.inv_bnorm = invb;
+    ca.rhs_state = rhs_state;
+    ca.k_final = k_final;
+    ca.all_done = &ctl->all_done;
+    ca.counter = &ctl->counter;
+    ca.k_dev = &ctl->k_dev;
+    ca.hist = hist_dev;
+    ca.outer_tol = o.outer_tol;
+    ca.outer_maxit = o.outer_maxit;
+
+    int chunk = o.check_every > 0 ? o.check_every : 4;
+    int* h_flags = nullptr;  // all_done, err
+    MS_CUDA(g, cudaMallocHost(&h_flags, 4 * sizeof(int)));
+    struct HostGuard {
+      int* p;
+      ~HostGuard() { cudaFreeHost(p); }
+    } hg{h_flags};
+    cudaGraphExec_t gexec = nullptr;
+    int gexec_len = 0;
+    struct GraphGuard {
+      cudaGraphExec_t* e;
+      ~GraphGuard() {
+        if (*e) cudaGraphExecDestroy(*e);
+      }
+    } gg{&gexec};
+    // optional per-sweep timing: one event pair per sweep of a chunk
+    std::vector<cudaEvent_t> pev;
+    struct EvVec {
+      std::vector<cudaEvent_t>* v;
+      ~EvVec() {
+        for (cudaEvent_t e : *v) cudaEventDestroy(e);
+      }
+    } pevg{&pev};
+    double sweep_ms = 0.0;
+    int sweeps_timed = 0;
+    auto t_start = std::chrono::steady_clock::now();
+    long long launched = 0;  // sweeps launched
+    for (;;) {
+      const long long remaining = (long long)o.outer_maxit + 1 - launched;
+      if (remaining <= 0) break;
+      const int n = (int)std::min<long long>(chunk, remaining);
+      if (o.profile) {
+        while ((int)pev.size() < 2 * n) {
+          cudaEvent_t e;
+          MS_CUDA(g, cudaEventCreate(&e));
+          pev.push_back(e);
+        }
+      }
+      auto one_sweep = [&](int i, cudaStream_t cs) -> cudaError_t {
+        cudaError_t ce = cudaSuccess;
+        if (o.profile) ce = cudaEventRecord(pev[2 * i], cs);
+        if (ce == cudaSuccess) ce = launch_sweep(prec, shape.threads, shape.cluster, shape.slots, sa, cs);
+        if (ce == cudaSuccess && o.profile) ce = cudaEventRecord(pev[2 * i + 1], cs);
+        if (ce == cudaSuccess) ce = launch_check(ca, cs);
+        return ce;
+      };
+      if (o.use_graph && n == chunk) {
+        if (!gexec || gexec_len != n) {
+          if (gexec) cudaGraphExecDestroy(gexec);
+          gexec = nullptr;
+          cudaStream_t cs;
+          MS_CUDA(g, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+          cudaGraph_t graph = nullptr;
+          cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+          for (int i = 0; i < n && ce == cudaSuccess; ++i) ce = one_sweep(i, cs);
+          cudaError_t ce2 = cudaStreamEndCapture(cs, &graph);
+          if (ce == cudaSuccess) ce = ce2;
+          if (ce == cudaSuccess) ce = cudaGraphInstantiate(&gexec, graph, 0);
+          if (graph) cudaGraphDestroy(graph);
+          cudaStreamDestroy(cs);
+          MS_CUDA(g, ce);
+          gexec_len = n;
+        }
+        MS_CUDA(g, cudaGraphLaunch(gexec, stream));
+      } else {
+        for (int i = 0; i < n; ++i) MS_CUDA(g, one_sweep(i, stream));
+      }
+      launched += n;
+      launches += 2 * n;
+      MS_CUDA(g, cudaMemcpyAsync(h_flags, &ctl->all_done, sizeof(int), cudaMemcpyDeviceToHost, stream));
+      MS_CUDA(g, cudaMemcpyAsync(h_flags + 1, &ctl->err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+      MS_CUDA(g, cudaStreamSynchronize(stream));
+      if (h_flags[1]) return fail(g, MS_ERR_CUDA, "ms_solve: device error word 0x%x", h_flags[1]);
+      if (o.profile) {
+        for (int i = 0; i < n; ++i) {
+          float t = 0.f;
+          MS_CUDA(g, cudaEventElapsedTime(&t, pev[2 * i], pev[2 * i + 1]));
+          sweep_ms += t;
+          sweeps_timed += 1;
+        }
+      }
+      if (h_flags[0]) break;
+      if (o.time_limit_ms > 0.0) {
+        double el = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+        if (el > o.time_limit_ms) {
+          status = MS_ERR_TIMEOUT;
+          break;
+        }
+      }
+      if (chunk < 16 && o.check_every == 0) chunk *= 2;
+    }
+    MS_CUDA(g, cudaMemcpyAsync(h_kfinal.data(), k_final, g->nrhs * sizeof(int), cudaMemcpyDeviceToHost, stream));
+    MS_CUDA(g, cudaMemcpyAsync(h_state.data(), rhs_state, g->nrhs * sizeof(int), cudaMemcpyDeviceToHost, stream));
+    MS_CUDA(g, cudaStreamSynchronize(stream));
+    if (status == MS_ERR_TIMEOUT) {
+      // stopped mid-solve: the latest complete iterate is x^k, k = sweeps launched (<= outer_maxit)
+      int kk = 0;
+      MS_CUDA(g, cudaMemcpy(&kk, &ctl->k_dev, sizeof(int), cudaMemcpyDeviceToHost));
+      for (int r = 0; r < g->nrhs; ++r)
+        if (h_state[r] == kActive) h_kfinal[r] = kk;
+    }
+    // move odd-k results into the caller's buffer
+    for (int r = 0; r < g->nrhs; ++r) {
+      if (h_kfinal[r] & 1)
+        MS_CUDA(g, cudaMemcpyAsync(x + (size_t)r * npts, g->xalt.as<double>() + (size_t)r * npts,
+                                   npts * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+      outer_max = std::max(outer_max, h_kfinal[r]);
+      if (h_state[r] == kStopped && status == MS_OK) status = MS_ERR_NOT_CONVERGED;
+    }
+    if (st) {
+      st->sweep_ms = sweep_ms;
+      st->sweep_launches = sweeps_timed;
+    }
+    if (o.res_hist) {
+      MS_CUDA(g, cudaMemcpyAsync(o.res_hist, hist_dev, (size_t)g->nrhs * (o.outer_maxit + 1) * sizeof(double),
+                                 cudaMemcpyDeviceToHost, stream));
+    }
+  }
+  MS_CUDA(g, cudaEventRecord(ev1, stream));
+  // final true residual
+  rc = run_resid(g, f, bnd, x, norms, nullptr, stream);
+  if (rc != MS_OK) return rc;
+  launches += 2;
+  std::vector<double> hn(2 * (size_t)g->nrhs);
+  std::vector<unsigned long long> hin(2 * (size_t)g->nrhs);
+  MS_CUDA(g, cudaMemcpyAsync(hn.data(), norms, hn.size() * sizeof(double), cudaMemcpyDeviceToHost, stream));
+  MS_CUDA(g, cudaMemcpyAsync(hin.data(), inner, hin.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                             stream));
+  MS_CUDA(g, cudaStreamSynchronize(stream));
+  MS_CUDA(g, cudaGetLastError());
+  if (st) {
+    float ms_el = 0.f;
+    cudaEventElapsedTime(&ms_el, ev0, ev1);
+    double relmax = 0.0;
+    long long inner_total = 0, inner_lups = 0;
+    for (int r = 0; r < g->nrhs; ++r) {
+      const double rel = hn[2 * r + 1] > 0.0 ? std::sqrt(hn[2 * r]) / std::sqrt(hn[2 * r + 1]) : std::sqrt(hn[2 * r]);
+      relmax = std::max(relmax, rel);
+      inner_total += (long long)hin[2 * r];
+      inner_lups += (long long)hin[2 * r + 1];
+      if (st->per_rhs_rel) st->per_rhs_rel[r] = rel;
+      if (o.mode == MS_MODE_SYNC && st->per_rhs_outer_its) st->per_rhs_outer_its[r] = h_kfinal[r];
+    }
+    // residual passes: sync mode forms one per sweep k = 0..K (the last one
+    // decides the stop), async mode one per block visit (st->lups on entry)
+    long long resid_lups = 0;
+    if (o.mode == MS_MODE_SYNC) {
+      for (int r = 0; r < g->nrhs; ++r) resid_lups += ((long long)h_kfinal[r] + 1) * npts;
+    } else {
+      resid_lups = st->lups;
+    }
+    st->status = status;
+    if (o.mode == MS_MODE_SYNC) st->outer_its = outer_max;
+    st->inner_its = inner_total;
+    st->lups = resid_lups + inner_lups;
+    st->rel_residual = relmax;
+    st->time_ms = ms_el;
+    st->launches = launches;
+    st->cluster = shape.cluster;
+    st->threads = shape.threads;
+    st->slots = shape.slots;
+  }
+  return status;
+}
+
+// ------------------------------------------------------------------ async solve
+// One persistent launch runs until the stale estimate says every rhs is below
+// tol (or caps are hit); the host then checks the true residual and, for any
+// rhs still above tol, re-arms it and relaunches from the current state.
+int solve_async(ms_grid* g, const double* f, const double* bnd, double* x, const ms_opts& o, ms_stats* st,
+                cudaStream_t stream, const LaunchShape& shape, const std::vector<Task>& tasks, long long maxpts,
+                double* invb_dev, int* rc_out) {
+  const int prec = o.precision == MS_PREC_MIXED ? 1 : 0;
+  const int ntasks = (int)tasks.size();
+  const int nblocks = g->px * g->py * g->pz;
+  long long face_stride = 0;
+  for (const Task& t : tasks)
+    face_stride = std::max({face_stride, (long long)t.bz * t.by, (long long)t.bz * t.bx, (long long)t.by * t.bx});
+  face_stride = (face_stride + 31) / 32 * 32;
+  std::vector<int> task_of((size_t)g->nrhs * nblocks, -1);
+  for (int i = 0; i < ntasks; ++i) task_of[(size_t)tasks[i].rhs * nblocks + tasks[i].block] = i;
+
+  // workspace layout (256-byte aligned pieces)
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o2 = off;
+    off += (bytes + 255) / 256 * 256;
+    return o2;
+  };
+  const size_t o_taskof = take(task_of.size() * sizeof(int));
+  const size_t o_faces = take((size_t)ntasks * 12 * face_stride * sizeof(double));
+  const size_t o_halo = take((size_t)ntasks * 12 * face_stride * sizeof(double));
+  const size_t o_seq = take((size_t)ntasks * 12 * sizeof(unsigned));
+  const size_t o_ver = take((size_t)ntasks * 6 * sizeof(unsigned));
+  const size_t o_hcur = take((size_t)ntasks * 6 * sizeof(int));
+  const size_t o_hver = take((size_t)ntasks * 6 * sizeof(unsigned));
+  const size_t o_part = take((size_t)ntasks * sizeof(double));
+  const size_t o_sweeps = take((size_t)ntasks * sizeof(int));
+  const size_t o_rstop = take((size_t)g->nrhs * sizeof(int));
+  const size_t o_flags = take(4 * sizeof(int));
+  MS_CUDA(g, g->async_ws.reserve(off));
+  char* w = g->async_ws.as<char>();
+  MS_CUDA(g, cudaMemsetAsync(w + o_seq, 0, o_part - o_seq, stream));  // seq, ver, hcur, hver
+  MS_CUDA(g, cudaMemsetAsync(w + o_rstop, 0, off - o_rstop, stream));
+  MS_CUDA(g, cudaMemcpyAsync(w + o_taskof, task_of.data(), task_of.size() * sizeof(int), cudaMemcpyHostToDevice,
+                             stream));
+  CtlLayout L = ctl_layout(g->nrhs);
+  char* ctlb = g->ctl.as<char>();
+  Ctl* ctl = reinterpret_cast<Ctl*>(ctlb);
+  unsigned long long* inner = reinterpret_cast<unsigned long long*>(ctlb + L.off_inner);
+
+  AsyncArgs a;
+  a.g = g->geo();
+  a.f = f;
+  a.bnd = bnd;
+  a.x = x;
+  a.tasks = g->tasks.as<Task>();
+  a.ntasks = ntasks;
+  a.px = g->px;
+  a.py = g->py;
+  a.pz = g->pz;
+  a.nblocks = nblocks;
+  a.task_of = reinterpret_cast<const int*>(w + o_taskof);
+  a.face_stride = face_stride;
+  a.faces = reinterpret_cast<double*>(w + o_faces);
+  a.face_seq = reinterpret_cast<unsigned*>(w + o_seq);
+  a.face_ver = reinterpret_cast<unsigned*>(w + o_ver);
+  a.halo = reinterpret_cast<double*>(w + o_halo);
+  a.halo_cur = reinterpret_cast<int*>(w + o_hcur);
+  a.halo_ver = reinterpret_cast<unsigned*>(w + o_hver);
+  a.partial = reinterpret_cast<double*>(w + o_part);
+  a.sweeps = reinterpret_cast<int*>(w + o_sweeps);
+  a.inv_bnorm = invb_dev;
+  a.rhs_stop = reinterpret_cast<int*>(w + o_rstop);
+  a.stop = reinterpret_cast<int*>(w + o_flags);
+  a.scratch = g->scratch.p;
+  a.vec_stride = (maxpts + 31) / 32 * 32;
+  a.inner_rtol = o.inner_rtol;
+  a.inner_maxit = o.inner_maxit;
+  a.outer_maxit = o.outer_maxit;
+  a.outer_tol = o.outer_tol;
+  a.slow_block = o.slow_block;
+  a.slow_ns = o.slow_ns;
+  a.inner_count = inner;
+  a.time_budget_ns = o.time_limit_ms > 0.0 ? (unsigned long long)(o.time_limit_ms * 1.0e6) : 0ull;
+  a.slice_ns = 2000000000ull;  // no single launch runs longer than ~2 s
+  a.err = &ctl->err;
+  MS_CUDA(g, launch_async_init(a, stream));
+
+  CtlLayout L2 = L;
+  double* norms = reinterpret_cast<double*>(ctlb + L2.off_norm);
+  std::vector<double> hn(2 * (size_t)g->nrhs);
+  std::vector<int> rstop(g->nrhs), sweeps(ntasks);
+  int launches = 1;
+  int status = MS_ERR_NOT_CONVERGED;
+  auto t_start = std::chrono::steady_clock::now();
+  for (int rel = 0; rel < 100000; ++rel) {
+    MS_CUDA(g, launch_async(prec, shape.threads, shape.cluster, shape.slots, a, stream));
+    launches += 1;
+    int rc = run_resid(g, f, bnd, x, norms, nullptr, stream);
+    if (rc != MS_OK) return rc;
+    launches += 2;
+    int herr = 0;
+    MS_CUDA(g, cudaMemcpyAsync(hn.data(), norms, hn.size() * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    MS_CUDA(g, cudaMemcpyAsync(sweeps.data(), a.sweeps, sweeps.size() * sizeof(int), cudaMemcpyDeviceToHost, stream));
+    MS_CUDA(g, cudaMemcpyAsync(&herr, a.err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    MS_CUDA(g, cudaStreamSynchronize(stream));
+    if (herr & kErrGeometry) return fail(g, MS_ERR_CUDA, "ms_solve: device error word 0x%x", herr);
+    bool all_ok = true;
+    for (int r = 0; r < g->nrhs; ++r) {
+      const double relr = hn[2 * r + 1] > 0.0 ? std::sqrt(hn[2 * r]) / std::sqrt(hn[2 * r + 1]) : std::sqrt(hn[2 * r]);
+      rstop[r] = relr < o.outer_tol ? 1 : 0;
+      if (!rstop[r]) all_ok = false;
+    }
+    if (all_ok) {
+      status = MS_OK;
+      break;
+    }
+    if (herr & kErrTimeout) {
+      status = MS_ERR_TIMEOUT;
+      break;
+    }
+    int min_sweeps = o.outer_maxit;
+    for (int i = 0; i < ntasks; ++i)
+      if (!rstop[tasks[i].rhs]) min_sweeps = std::min(min_sweeps, sweeps[i]);
+    if (min_sweeps >= o.outer_maxit) {
+      status = MS_ERR_NOT_CONVERGED;
+      break;
+    }
+    if (o.time_limit_ms > 0.0) {
+      double el = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+      if (el > o.time_limit_ms) {
+        status = MS_ERR_TIMEOUT;
+        break;
+      }
+      a.time_budget_ns = (unsigned long long)((o.time_limit_ms - el) * 1.0e6) + 1ull;
+    }
+    // re-arm the rhs whose true residual is still above tol
+    MS_CUDA(g, cudaMemcpyAsync(a.rhs_stop, rstop.data(), rstop.size() * sizeof(int), cudaMemcpyHostToDevice, stream));
+    MS_CUDA(g, cudaMemsetAsync(a.stop, 0, sizeof(int), stream));
+    MS_CUDA(g, launch_async_rearm(a, stream));
+    launches += 1;
+  }
+  *rc_out = status;
+  if (st) {
+    int mx = 0;
+    std::vector<int> per(g->nrhs, 0);
+    for (int i = 0; i < ntasks; ++i) {
+      mx = std::max(mx, sweeps[i]);
+      per[tasks[i].rhs] = std::max(per[tasks[i].rhs], sweeps[i]);
+    }
+    st->outer_its = mx;
+    if (st->per_rhs_outer_its)
+      for (int r = 0; r < g->nrhs; ++r) st->per_rhs_outer_its[r] = per[r];
+    long long lups = 0;
+    for (int i = 0; i < ntasks; ++i) lups += (long long)sweeps[i] * tasks[i].bx * tasks[i].by * tasks[i].bz;
+    st->lups = lups;  // residual passes; inner lattice updates are added by the caller
+    st->launches = launches;
+  }
+  return MS_OK;
+}

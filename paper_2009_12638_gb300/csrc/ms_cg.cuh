@@ -1,0 +1,145 @@
+// ms_cg.cuh -- the inner stage: conjugate gradients on one block system
+// A_ii d = r (sections 2.2 and 3 of the paper), run by one thread-block
+// cluster.  A_ii is the 7-point stencil restricted to the block, zero outside.
+//
+// Work split: the block (bx*by*bz points, x fastest, compact in a per-cluster
+// scratch slot) is cut into z-slabs, one per CTA of the cluster; inside a
+// slab a thread owns whole z-columns of the (x, y) plane and marches up z
+// keeping the column's neighbours in registers.  Each CG iteration is two
+// streaming passes over the slab with one cluster-wide reduction after each:
+//
+//   pass A: p_new = r + beta p_old at the point and its six neighbours
+//           (formed on the fly), q = A_ii p_new, store p_new, eta = p.q
+//   pass B: q = A_ii p_new again (recomputed, not stored), d += alpha p_new,
+//           r -= alpha q, gamma = r.r
+//
+// which moves 32 bytes per point per iteration at FP32 (r and p_old read,
+// p_new written; p_new read, d and r read and written).  p is double
+// buffered so pass A never reads what it writes.
+#pragma once
+#include "ms_device.cuh"
+
+namespace ms {
+
+template <typename T>
+struct CgVecs {
+  T* r;
+  T* p0;
+  T* p1;
+  T* d;
+};
+
+template <typename T>
+__device__ __forceinline__ CgVecs<T> slot_vecs(void* scratch, long long vec_stride, unsigned slot) {
+  T* base = reinterpret_cast<T*>(scratch) + (long long)slot * 4 * vec_stride;
+  return CgVecs<T>{base, base + vec_stride, base + 2 * vec_stride, base + 3 * vec_stride};
+}
+
+struct Slab {
+  int bx, by, bz, plane, z0, z1;
+};
+
+__device__ __forceinline__ Slab make_slab(int bx, int by, int bz, unsigned rank, unsigned csize) {
+  Slab s;
+  s.bx = bx;
+  s.by = by;
+  s.bz = bz;
+  s.plane = bx * by;
+  s.z0 = (int)(((long long)bz * rank) / csize);
+  s.z1 = (int)(((long long)bz * (rank + 1)) / csize);
+  return s;
+}
+
+// Shared memory used by the reductions of one cluster.
+struct RedSmem {
+  double slots[3][2][kMaxCluster];  // [phase][value][cta]: residual pair, eta, gamma
+  double wsum[2][32];
+};
+
+// Runs CG from d = 0 on r (gamma0 = r.r already reduced).  Returns the
+// number of iterations m; d holds the correction when m > 0.
+template <typename T, int NT>
+__device__ int block_cg(const CgVecs<T>& v, const Slab& sl, double gamma0, double inner_rtol, int inner_maxit,
+                        RedSmem& sm, unsigned rank, unsigned csize) {
+  if (!(gamma0 > 0.0)) return 0;
+  const int tid = threadIdx.x;
+  const int plane = sl.plane, bx = sl.bx, by = sl.by, bz = sl.bz, z0 = sl.z0, z1 = sl.z1;
+  double gamma = gamma0;
+  const double stop = inner_rtol * sqrt(gamma0);
+  double beta = 0.0;
+  int m = 0;
+  T* po = v.p0;
+  T* pn = v.p1;
+  T* const rv = v.r;  // written by pass B, read by pass A: plain coherent loads
+  while (m < inner_maxit) {
+    const bool first = (m == 0);
+    const T bT = (T)beta;
+    // ---------------- pass A
+    T eta_loc = 0;
+    for (int c = tid; c < plane; c += NT) {
+      const int x = c % bx, y = c / bx;
+      const bool xm = x > 0, xp = x < bx - 1, ym = y > 0, yp = y < by - 1;
+#define MS_PVAL(idx) (first ? rv[(idx)] : rv[(idx)] + bT * po[(idx)])
+      T pzm = (z0 > 0 && z0 < z1) ? MS_PVAL((z0 - 1) * plane + c) : (T)0;
+      T pc = (z0 < z1) ? MS_PVAL(z0 * plane + c) : (T)0;
+      for (int z = z0; z < z1; ++z) {
+        const int i = z * plane + c;
+        const T pzp = (z + 1 < bz) ? MS_PVAL(i + plane) : (T)0;
+        T s = pzm + pzp;
+        if (xm) s += MS_PVAL(i - 1);
+        if (xp) s += MS_PVAL(i + 1);
+        if (ym) s += MS_PVAL(i - bx);
+        if (yp) s += MS_PVAL(i + bx);
+        const T q = (T)6 * pc - s;
+        pn[i] = pc;
+        eta_loc += pc * q;
+        pzm = pc;
+        pc = pzp;
+      }
+#undef MS_PVAL
+    }
+    double red1[1] = {(double)eta_loc};
+    cluster_sum<NT, 1>(red1, sm.slots[1], sm.wsum, rank, csize);
+    const double eta = red1[0];
+    if (!(eta > 0.0)) break;  // curvature breakdown (or NaN): keep d from earlier steps
+    const double alpha = gamma / eta;
+    const T aT = (T)alpha;
+    // ---------------- pass B
+    T g_loc = 0;
+    for (int c = tid; c < plane; c += NT) {
+      const int x = c % bx, y = c / bx;
+      const bool xm = x > 0, xp = x < bx - 1, ym = y > 0, yp = y < by - 1;
+      T pzm = (z0 > 0 && z0 < z1) ? pn[(z0 - 1) * plane + c] : (T)0;
+      T pc = (z0 < z1) ? pn[z0 * plane + c] : (T)0;
+      for (int z = z0; z < z1; ++z) {
+        const int i = z * plane + c;
+        const T pzp = (z + 1 < bz) ? pn[i + plane] : (T)0;
+        T s = pzm + pzp;
+        if (xm) s += pn[i - 1];
+        if (xp) s += pn[i + 1];
+        if (ym) s += pn[i - bx];
+        if (yp) s += pn[i + bx];
+        const T q = (T)6 * pc - s;
+        v.d[i] = first ? aT * pc : v.d[i] + aT * pc;
+        const T rn = v.r[i] - aT * q;
+        v.r[i] = rn;
+        g_loc += rn * rn;
+        pzm = pc;
+        pc = pzp;
+      }
+    }
+    double red2[1] = {(double)g_loc};
+    cluster_sum<NT, 1>(red2, sm.slots[2], sm.wsum, rank, csize);
+    const double gnew = red2[0];
+    m += 1;
+    if (sqrt(gnew) <= stop) break;
+    beta = gnew / gamma;
+    gamma = gnew;
+    T* t = po;
+    po = pn;
+    pn = t;
+  }
+  return m;
+}
+
+}  // namespace ms

@@ -1,0 +1,119 @@
+// ms_device.cuh -- device building blocks shared by the sweep kernels:
+// thread-block-cluster primitives (DSMEM stores, cluster barrier), the
+// deterministic cluster-wide sum, and the stencil pieces of the residual.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "ms_internal.h"
+
+namespace ms {
+
+__device__ __forceinline__ unsigned cl_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cl_size() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cl_id() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cl_count() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+  return r;
+}
+
+// Full cluster barrier.  Release on arrive / acquire on wait make every
+// global and shared write issued before it by any CTA of the cluster visible
+// to every CTA of the cluster after it.
+__device__ __forceinline__ void cl_barrier() {
+  asm volatile(
+      "barrier.cluster.arrive.release.aligned;\n\t"
+      "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ unsigned cl_map(const void* local, unsigned rank) {
+  unsigned la = (unsigned)__cvta_generic_to_shared(local), ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(la), "r"(rank));
+  return ra;
+}
+__device__ __forceinline__ void cl_store(double* local, unsigned rank, double v) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(cl_map(local, rank)), "d"(v) : "memory");
+}
+__device__ __forceinline__ void cl_store(int* local, unsigned rank, int v) {
+  asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(cl_map(local, rank)), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ double warp_sum_to_lane0(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic cluster-wide sum of NV doubles per thread.  Every CTA ends
+// with bit-identical totals: each CTA's partial is formed once (lane 0 of
+// warp 0), stored into slot[rank] of every CTA, and every CTA adds the slots
+// in rank order.  `slots` is [NV][kMaxCluster] shared doubles that must not
+// be reused by another reduction before the next cluster barrier; `wsum` is
+// [NV][32] shared doubles.  Contains one cluster barrier.
+template <int NT, int NV>
+__device__ __forceinline__ void cluster_sum(double (&v)[NV], double (*slots)[kMaxCluster], double (*wsum)[32],
+                                            unsigned rank, unsigned csize) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int a = 0; a < NV; ++a) {
+    double w = warp_sum_to_lane0(v[a]);
+    if (lane == 0) wsum[a][warp] = w;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+      double w = (lane < NT / 32) ? wsum[a][lane] : 0.0;
+      w = warp_sum_to_lane0(w);
+      w = __shfl_sync(0xffffffffu, w, 0);
+      if (lane < (int)csize) cl_store(&slots[a][rank], (unsigned)lane, w);
+    }
+  }
+  cl_barrier();
+#pragma unroll
+  for (int a = 0; a < NV; ++a) {
+    double s = 0.0;
+    for (unsigned i = 0; i < csize; ++i) s += slots[a][i];
+    v[a] = s;
+  }
+}
+
+// Neighbour sums of interior grid point (gx, gy, gz) of one rhs: `inner`
+// gets the neighbours inside the grid, `outer` the Dirichlet values of the
+// neighbours on the boundary, read from the packed faces (bnd may be null:
+// zero data).  bhat = f + outer is the right-hand side with section 2.1's
+// boundary values lifted into it, applied on the fly; (A x) = 6 x - inner.
+__device__ __forceinline__ void nbr_sums(const Geo& g, const double* __restrict__ x, const double* __restrict__ bnd,
+                                         int gx, int gy, int gz, long long gi, double& inner, double& outer) {
+  const long long nxy = (long long)g.nx * g.ny;
+  const long long fyz = (long long)g.nz * g.ny, fxz = (long long)g.nz * g.nx;
+  double si = 0.0, so = 0.0;
+  if (gx > 0) si += x[gi - 1];
+  else if (bnd) so += bnd[(long long)gz * g.ny + gy];
+  if (gx < g.nx - 1) si += x[gi + 1];
+  else if (bnd) so += bnd[fyz + (long long)gz * g.ny + gy];
+  if (gy > 0) si += x[gi - g.nx];
+  else if (bnd) so += bnd[2 * fyz + (long long)gz * g.nx + gx];
+  if (gy < g.ny - 1) si += x[gi + g.nx];
+  else if (bnd) so += bnd[2 * fyz + fxz + (long long)gz * g.nx + gx];
+  if (gz > 0) si += x[gi - nxy];
+  else if (bnd) so += bnd[2 * fyz + 2 * fxz + (long long)gy * g.nx + gx];
+  if (gz < g.nz - 1) si += x[gi + nxy];
+  else if (bnd) so += bnd[2 * fyz + 2 * fxz + nxy + (long long)gy * g.nx + gx];
+  inner = si;
+  outer = so;
+}
+
+}  // namespace ms

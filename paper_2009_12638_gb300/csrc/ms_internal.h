@@ -1,0 +1,131 @@
+// ms_internal.h -- types shared by the host orchestration (ms_api.cu) and the
+// device kernels (ms_kernels.cu, ms_async.cu).  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace ms {
+
+constexpr int kMaxCluster = 16;
+
+// One unit of outer work: block `block` of right-hand side `rhs`.
+// (ox, oy, oz) is the block origin in the grid, (bx, by, bz) its edge lengths.
+struct Task {
+  int ox, oy, oz, bx, by, bz, rhs, block;
+};
+
+struct Geo {
+  int nx, ny, nz, nrhs;
+  long long npts;  // nx*ny*nz
+  long long nbnd;  // packed boundary doubles per rhs
+};
+
+// rhs_state values
+constexpr int kActive = 0;
+constexpr int kConverged = 1;
+constexpr int kStopped = 2;
+
+// device error word bits
+constexpr int kErrGeometry = 1;
+constexpr int kErrTimeout = 2;
+
+// Arguments of one synchronous outer sweep.  The sweep index k is read from
+// device memory (k_dev) so that a captured graph of sweeps can be replayed.
+struct SweepArgs {
+  Geo g;
+  const double* f;    // [nrhs][npts] or null
+  const double* bnd;  // [nrhs][nbnd] or null
+  double* xbuf0;      // x^k for even k
+  double* xbuf1;      // x^k for odd k
+  const Task* tasks;
+  int ntasks;
+  unsigned int* counter;  // dynamic task queue head, reset by the check kernel
+  const int* rhs_state;   // [nrhs]
+  const int* all_done;
+  double* partial;  // [ntasks] block sum of squares of b - A x^k
+  void* scratch;    // per cluster slot: r, p0, p1, d (vec_stride elements each)
+  long long vec_stride;
+  double inner_rtol;
+  int inner_maxit;
+  int outer_maxit;
+  const int* k_dev;
+  unsigned long long* inner_count;  // [nrhs][2]: inner iterations, inner lattice updates
+  int* err;
+};
+
+struct CheckArgs {
+  int nrhs;
+  int ntasks;
+  const Task* tasks;
+  const double* partial;
+  const double* inv_bnorm;  // [nrhs]
+  int* rhs_state;
+  int* k_final;  // [nrhs]
+  int* all_done;
+  unsigned int* counter;
+  int* k_dev;
+  double* hist;  // [nrhs][outer_maxit+1] or null
+  double outer_tol;
+  int outer_maxit;
+};
+
+// Asynchronous persistent solve (see ms_async.cu).  Task t = (block, rhs) is
+// owned by cluster t % nclusters for the whole launch.
+struct AsyncArgs {
+  Geo g;
+  const double* f;
+  const double* bnd;
+  double* x;          // [nrhs][npts], updated in place (each block only by its owner)
+  const Task* tasks;  // [ntasks]
+  int ntasks;
+  int px, py, pz, nblocks;
+  const int* task_of;      // [nrhs][nblocks] -> task index
+  long long face_stride;   // doubles per face slot (max face size)
+  double* faces;           // [ntasks][6][2][face_stride] published boundary layers of x
+  unsigned int* face_seq;  // [ntasks][6][2] seqlock counters (odd while a slot is written)
+  unsigned int* face_ver;  // [ntasks][6] number of publishes; latest slot = ver & 1
+  double* halo;            // [ntasks][6][2][face_stride] neighbour values in use / being fetched
+  int* halo_cur;           // [ntasks][6] which halo slot is in use
+  unsigned int* halo_ver;  // [ntasks][6] neighbour version held
+  double* partial;         // [ntasks] latest ||r_i||^2 of the task (racy, may be stale)
+  int* sweeps;             // [ntasks] local sweeps done
+  const double* inv_bnorm; // [nrhs]
+  int* rhs_stop;           // [nrhs] set when the stale estimate of that rhs is below tol
+  int* stop;               // all work stops (all rhs stopped, or time budget spent)
+  void* scratch;
+  long long vec_stride;
+  double inner_rtol;
+  int inner_maxit;
+  int outer_maxit;
+  double outer_tol;
+  int slow_block;
+  int slow_ns;
+  unsigned long long* inner_count;  // [nrhs][2]: iterations, lattice updates
+  unsigned long long time_budget_ns;  // 0 = none; when spent the launch stops with kErrTimeout
+  unsigned long long slice_ns;        // the launch returns (no error) after this long; the host relaunches
+  int* err;
+};
+
+struct ResidArgs {
+  Geo g;
+  const double* f;
+  const double* bnd;
+  const double* x;
+  double* part;  // [nrhs][nblk][2]: sum r^2, sum bhat^2
+  int nblk;
+};
+
+// launchers (ms_kernels.cu / ms_async.cu)
+cudaError_t launch_sweep(int prec, int threads, int cluster, int slots, const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_check(const CheckArgs& a, cudaStream_t s);
+cudaError_t sweep_max_clusters(int prec, int threads, int cluster, int* out);
+cudaError_t launch_async(int prec, int threads, int cluster, int slots, const AsyncArgs& a, cudaStream_t s);
+cudaError_t async_max_clusters(int prec, int threads, int cluster, int* out);
+cudaError_t launch_resid(const ResidArgs& a, double* out /*[nrhs][2]*/, double* inv_bnorm /*[nrhs] or null*/,
+                         cudaStream_t s);
+cudaError_t launch_face_gather(const Geo& g, const double* lam, double* grad, cudaStream_t s);
+cudaError_t launch_async_init(const AsyncArgs& a, cudaStream_t s);
+cudaError_t launch_async_rearm(const AsyncArgs& a, cudaStream_t s);
+
+}  // namespace ms

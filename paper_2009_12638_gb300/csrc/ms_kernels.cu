@@ -1,0 +1,317 @@
+// ms_kernels.cu -- synchronous outer sweep, convergence check, true residual
+// and the adjoint face gather.
+//
+// One synchronous outer sweep k (block Jacobi, section 3 of the paper; the
+// loop of Listing 1) is ONE launch of sweep_kernel: a grid of thread-block
+// clusters, each cluster a "slot" that pulls (block, rhs) tasks from a
+// queue.  For its task a cluster
+//   1. forms the block residual r = bhat - A x^k in FP64 from x^k (the halo
+//      is read straight from the neighbours' part of x^k: every block reads
+//      the same x^k, strict Jacobi) and the block partial ||r_i||^2;
+//   2. runs the inner CG on A_ii d = r (ms_cg.cuh) in T = float or double;
+//   3. writes x^{k+1}_i = x^k_i + d in FP64 into the other buffer.
+// x is double buffered, so the kernel boundary is the only grid-wide
+// synchronisation a sweep needs.  A one-CTA check kernel then sums the block
+// partials in a fixed order (section 3: the global residual is the square
+// root of the sum of the block sums of squares), applies the stop rule of
+// section 2.1 per rhs and advances the sweep counter kept in device memory,
+// so the same [sweep, check] pair can be replayed from a CUDA graph.
+//
+// Because the residual of x^k is formed inside sweep k, the stop decision for
+// x^k lands after sweep k's inner solves; the solver then returns x^k (still
+// in its buffer) and sweep k's update is discarded.
+#include <cuda_runtime.h>
+
+#include "ms_cg.cuh"
+#include "ms_device.cuh"
+#include "ms_internal.h"
+
+namespace ms {
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, 1) sweep_kernel(const SweepArgs a) {
+  __shared__ RedSmem sm;
+  __shared__ int s_task[2];
+  if (*a.all_done) return;
+  const unsigned rank = cl_rank(), csize = cl_size(), slot = cl_id();
+  const int tid = threadIdx.x;
+  const int k = *a.k_dev;
+  const double* __restrict__ xin = (k & 1) ? a.xbuf1 : a.xbuf0;
+  double* __restrict__ xout = (k & 1) ? a.xbuf0 : a.xbuf1;
+  const bool residual_only = (k >= a.outer_maxit);
+  const CgVecs<T> v = slot_vecs<T>(a.scratch, a.vec_stride, slot);
+  const Geo g = a.g;
+  const long long nxy = (long long)g.nx * g.ny;
+  int par = 0;
+  for (;;) {
+    if (rank == 0 && tid == 0) {
+      const int t = (int)atomicAdd(a.counter, 1u);
+      for (unsigned j = 0; j < csize; ++j) cl_store(&s_task[par], j, t);
+    }
+    cl_barrier();
+    const int t = s_task[par];
+    par ^= 1;
+    if (t >= a.ntasks) break;
+    const Task tk = a.tasks[t];
+    if (a.rhs_state[tk.rhs] != kActive) continue;
+    if ((long long)tk.bx * tk.by * tk.bz > a.vec_stride) {  // host guarantees this; never trust it blindly
+      if (tid == 0) atomicOr(a.err, kErrGeometry);
+      continue;
+    }
+    const Slab sl = make_slab(tk.bx, tk.by, tk.bz, rank, csize);
+    const long long rb = (long long)tk.rhs * g.npts;
+    const double* __restrict__ xr = xin + rb;
+    const double* __restrict__ fr = a.f ? a.f + rb : nullptr;
+    const double* __restrict__ br = a.bnd ? a.bnd + (long long)tk.rhs * g.nbnd : nullptr;
+    // ---- 1. block residual in FP64, stored as T
+    double red0[2] = {0.0, 0.0};
+    {
+      double s_loc = 0.0;
+      T g_loc = 0;
+      for (int c = tid; c < sl.plane; c += NT) {
+        const int gx = tk.ox + c % tk.bx, gy = tk.oy + c / tk.bx;
+        for (int z = sl.z0; z < sl.z1; ++z) {
+          const int gz = tk.oz + z;
+          const long long gi = (long long)gz * nxy + (long long)gy * g.nx + gx;
+          double si, so;
+          nbr_sums(g, xr, br, gx, gy, gz, gi, si, so);
+          const double bh = fr ? fr[gi] + so : so;
+          const double rr = bh - (6.0 * xr[gi] - si);
+          s_loc += rr * rr;
+          const T rt = (T)rr;
+          v.r[z * sl.plane + c] = rt;
+          g_loc += rt * rt;
+        }
+      }
+      red0[0] = s_loc;
+      red0[1] = (double)g_loc;
+    }
+    cluster_sum<NT, 2>(red0, sm.slots[0], sm.wsum, rank, csize);
+    if (rank == 0 && tid == 0) a.partial[t] = red0[0];
+    if (residual_only) continue;
+    // ---- 2. inner CG
+    const int m = block_cg<T, NT>(v, sl, red0[1], a.inner_rtol, a.inner_maxit, sm, rank, csize);
+    // ---- 3. outer update into the other buffer
+    double* __restrict__ xo = xout + rb;
+    for (int c = tid; c < sl.plane; c += NT) {
+      const int gx = tk.ox + c % tk.bx, gy = tk.oy + c / tk.bx;
+      for (int z = sl.z0; z < sl.z1; ++z) {
+        const long long gi = (long long)(tk.oz + z) * nxy + (long long)gy * g.nx + gx;
+        xo[gi] = (m > 0) ? xr[gi] + (double)v.d[z * sl.plane + c] : xr[gi];
+      }
+    }
+    if (rank == 0 && tid == 0 && m > 0) {
+      atomicAdd(a.inner_count + 2 * tk.rhs, (unsigned long long)m);
+      atomicAdd(a.inner_count + 2 * tk.rhs + 1, (unsigned long long)m * (unsigned long long)(sl.plane * tk.bz));
+    }
+  }
+}
+
+// One CTA: per-rhs global norm from the block partials (fixed task order),
+// stop rule, bookkeeping for the next sweep.
+__global__ void check_kernel(const CheckArgs a) {
+  const int k = *a.k_dev;
+  for (int s = threadIdx.x; s < a.nrhs; s += blockDim.x) {
+    if (a.rhs_state[s] != kActive) continue;
+    double sum = 0.0;
+    for (int t = 0; t < a.ntasks; ++t)
+      if (a.tasks[t].rhs == s) sum += a.partial[t];
+    const double rho = sqrt(sum) * a.inv_bnorm[s];
+    if (a.hist) a.hist[(long long)s * (a.outer_maxit + 1) + k] = rho;
+    if (rho < a.outer_tol) {
+      a.rhs_state[s] = kConverged;
+      a.k_final[s] = k;
+    } else if (k >= a.outer_maxit) {
+      a.rhs_state[s] = kStopped;
+      a.k_final[s] = k;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int done = 1;
+    for (int s = 0; s < a.nrhs; ++s)
+      if (a.rhs_state[s] == kActive) done = 0;
+    *a.all_done = done;
+    *a.counter = 0u;
+    *a.k_dev = k + 1;
+  }
+}
+
+// ---------------------------------------------------------------- true residual
+// grid (nblk, nrhs): per-CTA sums of r^2 and bhat^2, r = bhat - A x.
+__global__ void __launch_bounds__(256) resid_kernel(const ResidArgs a) {
+  const Geo g = a.g;
+  const int s = blockIdx.y;
+  const long long rb = (long long)s * g.npts;
+  const double* __restrict__ x = a.x + rb;
+  const double* __restrict__ f = a.f ? a.f + rb : nullptr;
+  const double* __restrict__ bnd = a.bnd ? a.bnd + (long long)s * g.nbnd : nullptr;
+  const long long nxy = (long long)g.nx * g.ny;
+  double sr = 0.0, sb = 0.0;
+  for (long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x; gi < g.npts;
+       gi += (long long)gridDim.x * blockDim.x) {
+    const int gx = (int)(gi % g.nx);
+    const int gy = (int)((gi / g.nx) % g.ny);
+    const int gz = (int)(gi / nxy);
+    double si, so;
+    nbr_sums(g, x, bnd, gx, gy, gz, gi, si, so);
+    const double bh = f ? f[gi] + so : so;
+    const double r = bh - (6.0 * x[gi] - si);
+    sr += r * r;
+    sb += bh * bh;
+  }
+  __shared__ double w[2][8];
+  sr = warp_sum_to_lane0(sr);
+  sb = warp_sum_to_lane0(sb);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    w[0][warp] = sr;
+    w[1][warp] = sb;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a0 = 0.0, a1 = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      a0 += w[0][i];
+      a1 += w[1][i];
+    }
+    a.part[((long long)s * a.nblk + blockIdx.x) * 2 + 0] = a0;
+    a.part[((long long)s * a.nblk + blockIdx.x) * 2 + 1] = a1;
+  }
+}
+
+__global__ void resid_finish_kernel(int nrhs, int nblk, const double* part, double* out, double* inv_bnorm) {
+  for (int s = threadIdx.x; s < nrhs; s += blockDim.x) {
+    double a0 = 0.0, a1 = 0.0;
+    for (int b = 0; b < nblk; ++b) {
+      a0 += part[((long long)s * nblk + b) * 2 + 0];
+      a1 += part[((long long)s * nblk + b) * 2 + 1];
+    }
+    out[2 * s + 0] = a0;
+    out[2 * s + 1] = a1;
+    if (inv_bnorm) inv_bnorm[s] = a1 > 0.0 ? 1.0 / sqrt(a1) : 1.0;
+  }
+}
+
+// ---------------------------------------------------------------- adjoint face gather
+__global__ void face_gather_kernel(const Geo g, const double* __restrict__ lam, double* __restrict__ grad) {
+  const long long total = g.nbnd * g.nrhs;
+  const long long fyz = (long long)g.nz * g.ny, fxz = (long long)g.nz * g.nx, fxy = (long long)g.ny * g.nx;
+  const long long nxy = (long long)g.nx * g.ny;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long s = e / g.nbnd;
+    long long p = e - s * g.nbnd;
+    int i, j, k;
+    if (p < 2 * fyz) {  // x- / x+ : (k, j)
+      const bool hi = p >= fyz;
+      const long long q = hi ? p - fyz : p;
+      k = (int)(q / g.ny);
+      j = (int)(q % g.ny);
+      i = hi ? g.nx - 1 : 0;
+    } else if ((p -= 2 * fyz) < 2 * fxz) {  // y- / y+ : (k, i)
+      const bool hi = p >= fxz;
+      const long long q = hi ? p - fxz : p;
+      k = (int)(q / g.nx);
+      i = (int)(q % g.nx);
+      j = hi ? g.ny - 1 : 0;
+    } else {  // z- / z+ : (j, i)
+      p -= 2 * fxz;
+      const bool hi = p >= fxy;
+      const long long q = hi ? p - fxy : p;
+      j = (int)(q / g.nx);
+      i = (int)(q % g.nx);
+      k = hi ? g.nz - 1 : 0;
+    }
+    grad[e] = lam[s * g.npts + (long long)k * nxy + (long long)j * g.nx + i];
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+template <typename T, int NT>
+static cudaError_t launch_sweep_t(int cluster, int slots, const SweepArgs& a, cudaStream_t s) {
+  auto kern = sweep_kernel<T, NT>;
+  if (cluster > 8) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(cluster * slots), 1, 1);
+  cfg.blockDim = dim3(NT, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)cluster;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+template <typename T, int NT>
+static cudaError_t max_clusters_t(int cluster, int* out) {
+  auto kern = sweep_kernel<T, NT>;
+  if (cluster > 8) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(cluster * 64), 1, 1);
+  cfg.blockDim = dim3(NT, 1, 1);
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)cluster;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaOccupancyMaxActiveClusters(out, kern, &cfg);
+}
+
+#define MS_DISPATCH(prec, threads, FN, ...)                                    \
+  do {                                                                         \
+    if (prec == 1) {                                                           \
+      if (threads == 256) return FN<float, 256>(__VA_ARGS__);                  \
+      if (threads == 512) return FN<float, 512>(__VA_ARGS__);                  \
+      if (threads == 1024) return FN<float, 1024>(__VA_ARGS__);                \
+    } else {                                                                   \
+      if (threads == 256) return FN<double, 256>(__VA_ARGS__);                 \
+      if (threads == 512) return FN<double, 512>(__VA_ARGS__);                 \
+      if (threads == 1024) return FN<double, 1024>(__VA_ARGS__);               \
+    }                                                                          \
+    return cudaErrorInvalidValue;                                              \
+  } while (0)
+
+cudaError_t launch_sweep(int prec, int threads, int cluster, int slots, const SweepArgs& a, cudaStream_t s) {
+  MS_DISPATCH(prec, threads, launch_sweep_t, cluster, slots, a, s);
+}
+
+cudaError_t sweep_max_clusters(int prec, int threads, int cluster, int* out) {
+  MS_DISPATCH(prec, threads, max_clusters_t, cluster, out);
+}
+
+cudaError_t launch_check(const CheckArgs& a, cudaStream_t s) {
+  check_kernel<<<1, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_resid(const ResidArgs& a, double* out, double* inv_bnorm, cudaStream_t s) {
+  resid_kernel<<<dim3((unsigned)a.nblk, (unsigned)a.g.nrhs), 256, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  resid_finish_kernel<<<1, 128, 0, s>>>(a.g.nrhs, a.nblk, a.part, out, inv_bnorm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_face_gather(const Geo& g, const double* lam, double* grad, cudaStream_t s) {
+  const long long total = g.nbnd * g.nrhs;
+  long long blocks = (total + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  face_gather_kernel<<<(unsigned)blocks, 256, 0, s>>>(g, lam, grad);
+  return cudaGetLastError();
+}
+
+}  // namespace ms

@@ -1,0 +1,36 @@
+// ms_tune.h -- launch-shape selection for the sweep kernels: CTAs per block
+// (cluster size), threads per CTA and blocks in flight (cluster slots).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "ms_internal.h"
+
+namespace ms {
+
+struct LaunchShape {
+  int cluster = 1;
+  int threads = 512;
+  int slots = 1;
+};
+
+struct Tuner {
+  // cache of maxActiveClusters per (prec, mode, threads, cluster)
+  std::map<std::tuple<int, int, int, int>, int> occ;
+  // measured best shape per problem signature
+  std::map<std::vector<long long>, LaunchShape> best;
+  void release() {
+    occ.clear();
+    best.clear();
+  }
+};
+
+// Picks a shape; explicit non-zero requests are honoured.  Returns a
+// cudaError_t value (0 on success).
+int choose_shape(Tuner& t, int prec, int mode, const std::vector<Task>& tasks, long long maxpts, int req_cluster,
+                 int req_threads, int req_slots, LaunchShape* out);
+
+}  // namespace ms

@@ -1,0 +1,147 @@
+"""CPU-side checks of the C ABI: the library builds, loads, exports every
+symbol include/ms.h declares, the ctypes mirrors match the C structs, and the
+argument checks that run before any device work reject bad input."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2009_12638_gb300 import _build, _lib, inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ms.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return _lib.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^MS_API\s+[\w\s\*]*?\b(ms_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_exports():
+    assert declared_functions() == sorted(_lib.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", _lib.LIB_PATH], capture_output=True, text=True, check=True)
+    exported = set(re.findall(r"\sT\s+(ms_\w+)", out.stdout))
+    for name in declared_functions():
+        assert name in exported, name
+        assert hasattr(lib, name)
+    # nothing but the ABI is exported
+    assert exported == set(declared_functions())
+
+
+def test_ctypes_structs_match_c_layout(tmp_path):
+    src = tmp_path / "layout.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "ms.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu\n", sizeof(ms_opts), offsetof(ms_opts, outer_tol), offsetof(ms_opts, res_hist),
+         offsetof(ms_opts, slow_ns), offsetof(ms_opts, time_limit_ms));
+  printf("%zu %zu %zu %zu\n", sizeof(ms_stats), offsetof(ms_stats, lups), offsetof(ms_stats, per_rhs_rel),
+         offsetof(ms_stats, slots));
+  return 0;
+}
+''')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    a, b = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:2]
+    O, S = _lib.Opts, _lib.Stats
+    assert [int(v) for v in a.split()] == [ctypes.sizeof(O), O.outer_tol.offset, O.res_hist.offset,
+                                          O.slow_ns.offset, O.time_limit_ms.offset]
+    assert [int(v) for v in b.split()] == [ctypes.sizeof(S), S.lups.offset, S.per_rhs_rel.offset, S.slots.offset]
+
+
+def test_default_opts(lib):
+    o = _lib.Opts()
+    lib.ms_default_opts(ctypes.byref(o))
+    assert (o.mode, o.precision, o.inner_rtol, o.inner_maxit, o.outer_tol) == (0, 1, 1e-6, 50, 1e-8)
+    assert o.slow_block == -1 and o.use_graph == 1
+
+
+def test_boundary_size(lib):
+    for n in [(1, 1, 1), (3, 4, 5), (384, 320, 256)]:
+        assert lib.ms_boundary_size(*n) == inputs.boundary_size(*n)
+
+
+def _grid(lib, *dims):
+    h = ctypes.c_void_p()
+    rc = lib.ms_create_grid(*dims, ctypes.byref(h))
+    return rc, h
+
+
+def test_create_rejects_bad_sizes(lib):
+    for dims in [(0, 4, 4, 1), (4, -1, 4, 1), (4, 4, 4, 0)]:
+        rc, h = _grid(lib, *dims)
+        assert rc == _lib.MS_ERR_ARG and not h.value
+        assert b"sizes" in lib.ms_last_error(None)
+
+
+def test_partition_equal_split_and_errors(lib):
+    rc, h = _grid(lib, 10, 7, 5, 2)
+    assert rc == 0
+    try:
+        assert lib.ms_partition(h, 3, 2, 5, None, None, None) == 0
+        cx, cy, cz = (ctypes.c_int * 4)(), (ctypes.c_int * 3)(), (ctypes.c_int * 6)()
+        assert lib.ms_get_cuts(h, cx, cy, cz) == 0
+        assert list(cx) == list(inputs.equal_cuts(10, 3))
+        assert list(cy) == list(inputs.equal_cuts(7, 2))
+        assert list(cz) == list(inputs.equal_cuts(5, 5))
+        bad = (ctypes.c_int * 4)(0, 5, 5, 10)
+        assert lib.ms_partition(h, 3, 1, 1, bad, None, None) == _lib.MS_ERR_ARG
+        assert b"strictly" in lib.ms_last_error(h)
+        wrong_end = (ctypes.c_int * 3)(0, 4, 9)
+        assert lib.ms_partition(h, 2, 1, 1, wrong_end, None, None) == _lib.MS_ERR_ARG
+        assert lib.ms_partition(h, 11, 1, 1, None, None, None) == _lib.MS_ERR_ARG
+        assert lib.ms_partition(h, 0, 1, 1, None, None, None) == _lib.MS_ERR_ARG
+        good = (ctypes.c_int * 3)(0, 3, 10)
+        assert lib.ms_partition(h, 2, 1, 1, good, None, None) == 0
+    finally:
+        lib.ms_destroy(h)
+
+
+def test_solve_rejects_bad_arguments_before_device_work(lib):
+    rc, h = _grid(lib, 4, 4, 4, 1)
+    try:
+        o = _lib.Opts()
+        lib.ms_default_opts(ctypes.byref(o))
+        assert lib.ms_solve(h, None, None, None, ctypes.byref(o), None, None) == _lib.MS_ERR_ARG
+        dummy = ctypes.c_void_p(16)  # never dereferenced: options are checked first
+        for field, value in [("mode", 7), ("precision", 3), ("inner_maxit", -1), ("threads", 100),
+                             ("cluster", 17), ("outer_tol", -1.0), ("time_limit_ms", -5.0)]:
+            o2 = _lib.Opts()
+            lib.ms_default_opts(ctypes.byref(o2))
+            setattr(o2, field, value)
+            assert lib.ms_solve(h, None, None, dummy, ctypes.byref(o2), None, None) == _lib.MS_ERR_ARG, field
+        assert lib.ms_residual(h, None, None, None, None, None) == _lib.MS_ERR_ARG
+        assert lib.ms_face_gather(h, None, None, None) == _lib.MS_ERR_ARG
+    finally:
+        lib.ms_destroy(h)
+    assert lib.ms_destroy(None) == 0
+
+
+def test_python_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    monkeypatch.setattr(_lib, "_lib", None)
+    with pytest.raises(ImportError):
+        _lib.load(str(tmp_path / "missing.so"))
+
+
+def test_inputs_uneven_cuts_rule():
+    rng = np.random.default_rng(12638)
+    cx = inputs.uneven_cuts(384, 5, 40, 96, rng)
+    cy = inputs.uneven_cuts(320, 6, 40, 96, rng)
+    cz = inputs.uneven_cuts(256, 4, 40, 96, rng)
+    for c, n, p in [(cx, 384, 5), (cy, 320, 6), (cz, 256, 4)]:
+        e = np.diff(c)
+        assert c[0] == 0 and c[-1] == n and len(e) == p and e.min() >= 40 and e.max() <= 96

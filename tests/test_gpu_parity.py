@@ -1,0 +1,274 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances, derived from the arithmetic:
+* FP64 path, same algorithm, different rounding order: iterates after a few
+  sweeps agree to ~1e-13 relative; converged solutions must agree within
+  1e-9 relative in the inf-norm with the same outer count +-1.
+* Mixed path (FP32 inner CG, FP64 outer): it is a different inner
+  arithmetic, so iterates are not compared; the converged solution must reach
+  the same true relative residual (< tol) and lie within kappa(A) * tol of the
+  oracle's converged solution.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2009_12638_gb300 import Grid, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def cuda(a):
+    return None if a is None else torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def make_grid(nx, ny, nz, nrhs, cx, cy, cz):
+    g = Grid(nx, ny, nz, nrhs)
+    g.partition(len(cx) - 1, len(cy) - 1, len(cz) - 1, cx, cy, cz)
+    return g
+
+
+def rel_inf(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def oracle_all(cfg, **kw):
+    outs = []
+    for s in range(cfg["nrhs"]):
+        f = None if cfg.get("f") is None else cfg["f"][s]
+        outs.append(oracle.solve(cfg["nx"], cfg["ny"], cfg["nz"], cfg["cx"], cfg["cy"], cfg["cz"], f=f,
+                                 bnd=cfg["bnd"][s], **kw))
+    return outs
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _threads():
+    oracle.set_threads(min(16, oracle.max_threads()))
+    yield
+    oracle.set_threads(1)
+
+
+# ---------------------------------------------------------------- converged parity
+@pytest.mark.parametrize("cluster,threads", [(0, 0), (1, 256), (4, 512), (8, 1024)])
+def test_laplace32_fp64_sync_matches_oracle(cluster, threads):
+    cfg = inputs.make_config("laplace32_linear")
+    ref = oracle_all(cfg, history=True, **cfg["opts"])[0]
+    g = make_grid(cfg["nx"], cfg["ny"], cfg["nz"], 1, cfg["cx"], cfg["cy"], cfg["cz"])
+    x, st = g.solve(bnd=cuda(cfg["bnd"]), precision="fp64", cluster=cluster, threads=threads, history=True,
+                    **cfg["opts"])
+    assert st.status == 0 and ref["status"] == 0
+    assert abs(st.outer_its - ref["outer_its"]) <= 1
+    assert rel_inf(x.cpu().numpy()[0], ref["x"]) <= 1e-9
+    k = min(st.outer_its, ref["outer_its"])
+    np.testing.assert_allclose(st.history[0][: k + 1], ref["history"][: k + 1], rtol=1e-7)
+    # the closed form: u = x + 2y + 3z sampled on the grid solves the discrete problem
+    assert rel_inf(x.cpu().numpy()[0], cfg["exact"][0]) <= 440 * 1e-8
+
+
+def test_laplace32_mixed_sync_reaches_tolerance():
+    cfg = inputs.make_config("laplace32_linear")
+    ref = oracle_all(cfg, **cfg["opts"])[0]
+    g = make_grid(cfg["nx"], cfg["ny"], cfg["nz"], 1, cfg["cx"], cfg["cy"], cfg["cz"])
+    x, st = g.solve(bnd=cuda(cfg["bnd"]), precision="mixed", **cfg["opts"])
+    assert st.status == 0 and st.rel_residual < 1e-8
+    # independent re-check of the residual through ms_residual
+    assert g.residual(x, bnd=cuda(cfg["bnd"]))[0] < 1e-8
+    # kappa(A) ~ 440 at 32^3: both solutions lie within kappa * tol of the exact one
+    assert rel_inf(x.cpu().numpy()[0], ref["x"]) <= 2 * 440 * 1e-8
+    assert abs(st.outer_its - ref["outer_its"]) <= max(3, ref["outer_its"] // 20)
+
+
+# ---------------------------------------------------------------- first sweeps, bit-close
+def first_sweeps_case(nx, ny, nz, cx, cy, cz, nrhs, sweeps, seed, f=False, x0=False, inner_maxit=50, inner_rtol=1e-6,
+                      **solve_kw):
+    r = np.random.default_rng(seed)
+    bnd = r.uniform(-1, 1, size=(nrhs, inputs.boundary_size(nx, ny, nz)))
+    ff = r.standard_normal((nrhs, nz, ny, nx)) if f else None
+    xx = r.standard_normal((nrhs, nz, ny, nx)) if x0 else np.zeros((nrhs, nz, ny, nx))
+    g = make_grid(nx, ny, nz, nrhs, cx, cy, cz)
+    x, st = g.solve(f=cuda(ff), bnd=cuda(bnd), x0=cuda(xx), precision="fp64", outer_tol=0.0, outer_maxit=sweeps,
+                    inner_maxit=inner_maxit, inner_rtol=inner_rtol, **solve_kw)
+    assert st.status == 4 and st.outer_its == sweeps
+    xg = x.cpu().numpy()
+    for s in range(nrhs):
+        ref = oracle.solve(nx, ny, nz, cx, cy, cz, f=None if ff is None else ff[s], bnd=bnd[s], x0=xx[s],
+                           outer_tol=0.0, outer_maxit=sweeps, inner_maxit=inner_maxit, inner_rtol=inner_rtol)
+        assert rel_inf(xg[s], ref["x"]) <= 1e-11, s
+
+
+@pytest.mark.parametrize("case", [
+    # (nx, ny, nz, cx, cy, cz): several tiles, ragged tails, thin and single blocks
+    (37, 29, 23, [0, 13, 37], [0, 10, 20, 29], [0, 23]),
+    (20, 20, 20, [0, 7, 14, 20], [0, 20], [0, 1, 2, 19, 20]),
+    (9, 8, 7, list(range(10)), list(range(9)), list(range(8))),   # 1^3 blocks: point Jacobi
+    (33, 1, 1, [0, 16, 33], [0, 1], [0, 1]),                       # 1-D
+    (64, 48, 40, [0, 40, 64], [0, 17, 48], [0, 13, 27, 40]),
+])
+def test_first_sweeps_match_oracle_ragged(case):
+    nx, ny, nz, cx, cy, cz = case
+    first_sweeps_case(nx, ny, nz, cx, cy, cz, 1, 3, 21, f=True, x0=True)
+
+
+@pytest.mark.parametrize("cluster,threads", [(1, 256), (2, 512), (3, 256), (8, 512), (16, 256)])
+def test_first_sweeps_every_launch_shape(cluster, threads):
+    first_sweeps_case(24, 20, 33, [0, 11, 24], [0, 20], [0, 5, 33], 1, 2, 22, f=True, cluster=cluster,
+                      threads=threads)
+
+
+def test_first_sweeps_multi_rhs_uneven():
+    cfg = inputs.make_config("batched_uneven", scale=4)
+    first_sweeps_case(cfg["nx"], cfg["ny"], cfg["nz"], cfg["cx"], cfg["cy"], cfg["cz"], 3, 2, 23)
+
+
+def test_first_sweeps_without_graph_and_small_chunks():
+    first_sweeps_case(16, 16, 16, [0, 8, 16], [0, 8, 16], [0, 8, 16], 2, 5, 24, use_graph=False, check_every=1)
+    first_sweeps_case(16, 16, 16, [0, 8, 16], [0, 8, 16], [0, 8, 16], 2, 5, 24, use_graph=True, check_every=3)
+
+
+def test_inner_maxit_zero_and_one():
+    first_sweeps_case(12, 12, 12, [0, 6, 12], [0, 12], [0, 12], 1, 2, 25, inner_maxit=1)
+    g = make_grid(8, 8, 8, 1, [0, 4, 8], [0, 8], [0, 8])
+    bnd = np.random.default_rng(26).uniform(-1, 1, size=(1, inputs.boundary_size(8, 8, 8)))
+    x, st = g.solve(bnd=cuda(bnd), precision="fp64", inner_maxit=0, outer_maxit=3, outer_tol=1e-8)
+    assert st.status == 4 and not x.any()
+
+
+# ---------------------------------------------------------------- stop rule edges
+def test_zero_rhs_returns_zero_at_k0():
+    g = make_grid(10, 10, 10, 2, [0, 5, 10], [0, 10], [0, 10])
+    for prec in ("fp64", "mixed"):
+        x, st = g.solve(bnd=torch.zeros(2, g.nbnd, dtype=torch.float64, device="cuda"), precision=prec)
+        assert st.status == 0 and st.outer_its == 0 and not x.any()
+
+
+def test_exact_start_stops_at_k0():
+    n = 12
+    bnd = inputs.boundary_from_function(n, n, n, inputs.harmonic_xyz)[None]
+    x0 = inputs.interior_from_function(n, n, n, inputs.harmonic_xyz)[None]
+    g = make_grid(n, n, n, 1, [0, 6, 12], [0, 6, 12], [0, 12])
+    x, st = g.solve(bnd=cuda(bnd), x0=cuda(x0), precision="mixed")
+    assert st.status == 0 and st.outer_its == 0
+    np.testing.assert_array_equal(x.cpu().numpy(), x0)
+
+
+def test_outer_maxit_zero():
+    g = make_grid(6, 6, 6, 1, [0, 3, 6], [0, 6], [0, 6])
+    bnd = np.random.default_rng(27).uniform(-1, 1, size=(1, inputs.boundary_size(6, 6, 6)))
+    x, st = g.solve(bnd=cuda(bnd), precision="fp64", outer_maxit=0, history=True)
+    assert st.status == 4 and st.outer_its == 0 and not x.any()
+    assert st.history[0][0] == pytest.approx(1.0, rel=1e-14)
+
+
+def test_per_rhs_independent_stopping():
+    """Two rhs: one already solved by x0, one not; each stops on its own."""
+    n = 12
+    c = inputs.equal_cuts(n, 2)
+    b0 = inputs.boundary_from_function(n, n, n, inputs.harmonic_linear)
+    b1 = inputs.boundary_uniform(n, n, n, 1, 28)[0]
+    x0 = np.zeros((2, n, n, n))
+    x0[0] = inputs.interior_from_function(n, n, n, inputs.harmonic_linear)
+    g = make_grid(n, n, n, 2, c, c, c)
+    x, st = g.solve(bnd=cuda(np.stack([b0, b1])), x0=cuda(x0), precision="fp64")
+    ref = oracle.solve(n, n, n, c, c, c, bnd=b1)
+    assert st.per_rhs_outer_its[0] == 0
+    assert abs(st.per_rhs_outer_its[1] - ref["outer_its"]) <= 1
+    assert rel_inf(x.cpu().numpy()[1], ref["x"]) <= 1e-9
+    np.testing.assert_array_equal(x.cpu().numpy()[0], x0[0])
+
+
+# ---------------------------------------------------------------- residual / face gather
+def test_residual_matches_oracle():
+    nx, ny, nz = 19, 17, 13
+    r = np.random.default_rng(29)
+    bnd = r.standard_normal((2, inputs.boundary_size(nx, ny, nz)))
+    f = r.standard_normal((2, nz, ny, nx))
+    x = r.standard_normal((2, nz, ny, nx))
+    g = Grid(nx, ny, nz, 2)
+    got = g.residual(cuda(x), f=cuda(f), bnd=cuda(bnd))
+    for s in range(2):
+        bh = oracle.lift(nx, ny, nz, f[s], bnd[s])
+        want = np.linalg.norm(oracle.residual(bh, x[s])) / np.linalg.norm(bh)
+        assert got[s] == pytest.approx(want, rel=1e-12)
+    # zero bhat: absolute norm
+    got0 = g.residual(cuda(x))
+    for s in range(2):
+        assert got0[s] == pytest.approx(np.linalg.norm(oracle.apply_A(x[s])), rel=1e-12)
+
+
+def test_face_gather_is_lift_transpose():
+    """<lift(g), lam> = <g, gather(lam)> for all g, lam (the gather is the adjoint of the lift)."""
+    nx, ny, nz = 7, 6, 5
+    r = np.random.default_rng(30)
+    lam = r.standard_normal((1, nz, ny, nx))
+    gb = Grid(nx, ny, nz, 1).face_gather(cuda(lam)).cpu().numpy()[0]
+    nb = inputs.boundary_size(nx, ny, nz)
+    for _ in range(5):
+        gv = r.standard_normal(nb)
+        lhs = np.vdot(oracle.lift(nx, ny, nz, None, gv), lam[0])
+        assert np.vdot(gv, gb) == pytest.approx(lhs, rel=1e-12)
+
+
+# ---------------------------------------------------------------- host-buffer entry point
+def test_solve_host_matches_device():
+    n = 16
+    c = inputs.equal_cuts(n, 2)
+    bnd = inputs.boundary_uniform(n, n, n, 2, 31)
+    g = make_grid(n, n, n, 2, c, c, c)
+    xd, sd = g.solve(bnd=cuda(bnd), precision="fp64")
+    xh = np.zeros((2, n, n, n))
+    xh, sh = g.solve_host(bnd=bnd, x=xh, precision="fp64")
+    assert sd.status == 0 and sh.status == 0 and sd.outer_its == sh.outer_its
+    np.testing.assert_array_equal(xh, xd.cpu().numpy())
+
+
+# ---------------------------------------------------------------- asynchronous mode
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_async_converges_to_oracle_solution(prec):
+    cfg = inputs.make_config("laplace32_linear")
+    ref = oracle_all(cfg, **cfg["opts"])[0]
+    g = make_grid(cfg["nx"], cfg["ny"], cfg["nz"], 1, cfg["cx"], cfg["cy"], cfg["cz"])
+    x, st = g.solve(bnd=cuda(cfg["bnd"]), precision=prec, mode="async", **cfg["opts"])
+    assert st.status == 0 and st.rel_residual < 1e-8
+    assert g.residual(x, bnd=cuda(cfg["bnd"]))[0] < 1e-8
+    assert rel_inf(x.cpu().numpy()[0], ref["x"]) <= 2 * 440 * 1e-8
+
+
+def test_async_multi_rhs_uneven():
+    cfg = inputs.make_config("batched_uneven", scale=4)
+    g = make_grid(cfg["nx"], cfg["ny"], cfg["nz"], 16, cfg["cx"], cfg["cy"], cfg["cz"])
+    x, st = g.solve(bnd=cuda(cfg["bnd"]), precision="mixed", mode="async")
+    assert st.status == 0 and max(st.per_rhs_rel) < 1e-8
+    assert (g.residual(x, bnd=cuda(cfg["bnd"])) < 1e-8).all()
+
+
+def test_async_tolerates_a_slow_block():
+    """Section 5: asynchronous block Jacobi keeps progressing when one block is slow."""
+    n = 24
+    c = inputs.equal_cuts(n, 2)
+    bnd = inputs.boundary_uniform(n, n, n, 1, 32)
+    g = make_grid(n, n, n, 1, c, c, c)
+    x, st = g.solve(bnd=cuda(bnd), precision="mixed", mode="async", slow_block=3, slow_ns=200_000)
+    assert st.status == 0 and st.rel_residual < 1e-8
+
+
+def test_async_time_limit_returns_timeout():
+    n = 32
+    c = inputs.equal_cuts(n, 4)
+    bnd = inputs.boundary_uniform(n, n, n, 1, 33)
+    g = make_grid(n, n, n, 1, c, c, c)
+    x, st = g.solve(bnd=cuda(bnd), precision="fp64", mode="async", outer_tol=1e-14, time_limit_ms=20.0,
+                    slow_block=0, slow_ns=1_000_000)
+    assert st.status == 5
+    assert np.isfinite(x.cpu().numpy()).all()
+
+
+def test_sync_time_limit_returns_timeout():
+    n = 32
+    c = inputs.equal_cuts(n, 4)
+    bnd = inputs.boundary_uniform(n, n, n, 1, 34)
+    g = make_grid(n, n, n, 1, c, c, c)
+    x, st = g.solve(bnd=cuda(bnd), precision="fp64", outer_tol=1e-15, time_limit_ms=5.0, check_every=1)
+    assert st.status == 5
+    # the returned iterate is a complete sweep: its true residual is what the stats say
+    assert g.residual(x, bnd=cuda(bnd))[0] == pytest.approx(st.rel_residual, rel=1e-12)
