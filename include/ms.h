@@ -88,6 +88,9 @@ typedef struct {
   double* res_hist;      /* HOST, optional: [nrhs][outer_maxit+1] relative residual per sweep
                             (sync mode; entries after each rhs stops are left untouched) */
   int profile;           /* sync mode: time every sweep kernel with CUDA events (stats.sweep_ms) */
+  int engine;            /* inner-CG engine: 0 auto, 1 streaming (CG vectors in a global scratch slot
+                            per cluster, any block size, FP32 or FP64), 2 resident (CG vectors in
+                            registers and shared memory of the cluster; MIXED + SYNC, blocks that fit) */
 } ms_opts;
 
 typedef struct {

@@ -66,7 +66,7 @@ def _stream_handle(device):
 
 def _make_opts(lib, mode="sync", precision="mixed", inner_rtol=1e-6, inner_maxit=50, outer_tol=1e-8,
                outer_maxit=100000, time_limit_ms=0.0, cluster=0, threads=0, slots=0, check_every=0, use_graph=True,
-               slow_block=-1, slow_ns=0, profile=False):
+               slow_block=-1, slow_ns=0, profile=False, engine="auto"):
     o = _lib.Opts()
     lib.ms_default_opts(ctypes.byref(o))
     o.mode = _lib.MODE[mode] if isinstance(mode, str) else int(mode)
@@ -84,6 +84,7 @@ def _make_opts(lib, mode="sync", precision="mixed", inner_rtol=1e-6, inner_maxit
     o.slow_block = int(slow_block)
     o.slow_ns = int(slow_ns)
     o.profile = 1 if profile else 0
+    o.engine = {"auto": 0, "streaming": 1, "resident": 2}[engine] if isinstance(engine, str) else int(engine)
     return o
 
 
@@ -169,7 +170,8 @@ class Grid:
         x0: initial guess (default zero); out: optional result tensor (may be x0).
         opts: mode ('sync'|'async'), precision ('mixed'|'fp64'), inner_rtol,
         inner_maxit, outer_tol, outer_maxit, time_limit_ms, cluster, threads,
-        slots, check_every, use_graph, slow_block, slow_ns, profile.
+        slots, check_every, use_graph, slow_block, slow_ns, profile,
+        engine ('auto'|'streaming'|'resident').
         """
         f = self._field(f, "f", self.shape)
         bnd = self._field(bnd, "bnd", (self.nrhs, self.nbnd))

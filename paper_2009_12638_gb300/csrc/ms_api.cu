@@ -100,9 +100,11 @@ static int fail(ms_grid* g, int code, const char* fmt, ...) {
 #define MS_CUDA(g, expr)                                                                        \
   do {                                                                                          \
     cudaError_t e_ = (expr);                                                                    \
-    if (e_ != cudaSuccess)                                                                      \
+    if (e_ != cudaSuccess) {                                                                    \
+      cudaGetLastError(); /* clear a non-sticky error so later calls do not report it */       \
       return fail((g), e_ == cudaErrorMemoryAllocation ? MS_ERR_OOM : MS_ERR_CUDA, "%s: %s (%s)", \
                   #expr, cudaGetErrorName(e_), cudaGetErrorString(e_));                         \
+    }                                                                                           \
   } while (0)
 
 extern "C" long long ms_boundary_size(int nx, int ny, int nz) {
@@ -128,6 +130,7 @@ extern "C" void ms_default_opts(ms_opts* o) {
   o->slow_ns = 0;
   o->res_hist = nullptr;
   o->profile = 0;
+  o->engine = 0;
 }
 
 static std::vector<int> equal_cuts(int n, int p) {
@@ -234,6 +237,7 @@ static int check_opts(ms_grid* g, const ms_opts& o) {
     return fail(g, MS_ERR_ARG, "opts.threads must be 0, 256, 512 or 1024");
   if (o.slots < 0 || o.check_every < 0) return fail(g, MS_ERR_ARG, "opts.slots and opts.check_every must be >= 0");
   if (o.time_limit_ms < 0.0) return fail(g, MS_ERR_ARG, "opts.time_limit_ms must be >= 0");
+  if (o.engine < 0 || o.engine > 2) return fail(g, MS_ERR_ARG, "opts.engine must be 0 (auto), 1 or 2");
   return MS_OK;
 }
 
@@ -285,6 +289,7 @@ extern "C" int ms_solve(ms_grid* g, const double* f, const double* bnd, double* 
   else ms_default_opts(&o);
   int rc = check_opts(g, o);
   if (rc != MS_OK) return rc;
+  cudaGetLastError();  // a stale non-sticky error from unrelated work must not fail this solve
   return solve_device(g, f, bnd, x, o, stats, (cudaStream_t)stream);
 }
 
@@ -391,13 +396,13 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
 
   // launch shape
   LaunchShape shape;
-  int rc = choose_shape(g->tuner, prec, o.mode, tasks, maxpts, o.cluster, o.threads, o.slots, &shape);
+  int rc = choose_shape(g->tuner, prec, o.mode, o.engine, tasks, maxpts, o.cluster, o.threads, o.slots, &shape);
   if (rc != 0) return fail(g, MS_ERR_CUDA, "ms_solve: no launchable shape (%s)", cudaGetErrorString((cudaError_t)rc));
 
   // workspace
   const long long vec_stride = (maxpts + 31) / 32 * 32;
   CtlLayout L = ctl_layout(g->nrhs);
-  MS_CUDA(g, g->scratch.reserve((size_t)shape.slots * 4 * vec_stride * esz));
+  if (shape.variant < 0) MS_CUDA(g, g->scratch.reserve((size_t)shape.slots * 4 * vec_stride * esz));
   MS_CUDA(g, g->tasks.reserve(tasks.size() * sizeof(Task)));
   MS_CUDA(g, g->partial.reserve((size_t)ntasks * sizeof(double)));
   MS_CUDA(g, g->ctl.reserve(L.bytes));
@@ -453,6 +458,7 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
     sa.outer_maxit = o.outer_maxit;
     sa.k_dev = &ctl->k_dev;
     sa.inner_count = inner;
+    sa.inv_bnorm = invb;
     sa.err = &ctl->err;
     CheckArgs ca;
     ca.nrhs = g->nrhs;
@@ -510,12 +516,15 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
       auto one_sweep = [&](int i, cudaStream_t cs) -> cudaError_t {
         cudaError_t ce = cudaSuccess;
         if (o.profile) ce = cudaEventRecord(pev[2 * i], cs);
-        if (ce == cudaSuccess) ce = launch_sweep(prec, shape.threads, shape.cluster, shape.slots, sa, cs);
+        if (ce == cudaSuccess)
+          ce = shape.variant >= 0 ? launch_res_sweep(shape.variant, shape.cluster, shape.slots, shape.smem, sa, cs)
+                                  : launch_sweep(prec, shape.threads, shape.cluster, shape.slots, sa, cs);
         if (ce == cudaSuccess && o.profile) ce = cudaEventRecord(pev[2 * i + 1], cs);
         if (ce == cudaSuccess) ce = launch_check(ca, cs);
         return ce;
       };
-      if (o.use_graph && n == chunk) {
+      // (event timing is not available from graph-recorded events: profile runs launch directly)
+      if (o.use_graph && !o.profile && n == chunk) {
         if (!gexec || gexec_len != n) {
           if (gexec) cudaGraphExecDestroy(gexec);
           gexec = nullptr;

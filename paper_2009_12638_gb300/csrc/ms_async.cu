@@ -263,6 +263,8 @@ __global__ void __launch_bounds__(NT, 1) async_kernel(const AsyncArgs a) {
     }
 
     // ---------------- 2. block residual from own x and the halo, FP64
+    // (FP32 inner: r times a power of two ~ 1/||bhat||, undone in the update)
+    const double scale = inner_scale<T>(a.inv_bnorm[tk.rhs]), unscale = 1.0 / scale;
     const Slab sl = make_slab(tk.bx, tk.by, tk.bz, rank, csize);
     const long long rb = (long long)tk.rhs * g.npts;
     double* xr = a.x + rb;
@@ -307,7 +309,7 @@ __global__ void __launch_bounds__(NT, 1) async_kernel(const AsyncArgs a) {
           const double bh = fr ? fr[gi] + so : so;
           const double rr = bh - (6.0 * xr[gi] - si);
           s_loc += rr * rr;
-          const T rt = (T)rr;
+          const T rt = (T)(rr * scale);
           v.r[z * sl.plane + c] = rt;
           g_loc += rt * rt;
         }
@@ -315,7 +317,12 @@ __global__ void __launch_bounds__(NT, 1) async_kernel(const AsyncArgs a) {
       red0[0] = s_loc;
       red0[1] = (double)g_loc;
     }
-    cluster_sum<NT, 2>(red0, sm.slots[0], sm.wsum, rank, csize);
+    cluster_reduce<NT, 2>(red0, sm.slots[0], sm.wsum, rank, csize, [&](double (&t)[2]) {
+      sm.tot[0] = t[0];
+      sm.tot[1] = t[1];
+    });
+    red0[0] = sm.tot[0];
+    red0[1] = sm.tot[1];
     if (rank == 0 && tid == 0) st_rlx_f64(a.partial + t, red0[0]);
 
     // ---------------- 3. inner CG
@@ -345,7 +352,7 @@ __global__ void __launch_bounds__(NT, 1) async_kernel(const AsyncArgs a) {
       const int gx = tk.ox + x, gy = tk.oy + y;
       for (int z = sl.z0; z < sl.z1; ++z) {
         const long long gi = (long long)(tk.oz + z) * nxy + (long long)gy * g.nx + gx;
-        const double xn = (m > 0) ? xr[gi] + (double)v.d[z * sl.plane + c] : xr[gi];
+        const double xn = (m > 0) ? xr[gi] + (double)v.d[z * sl.plane + c] * unscale : xr[gi];
         xr[gi] = xn;
         if (x == 0 && fslot[0] >= 0) a.faces[(((long long)t * 6 + 0) * 2 + fslot[0]) * fs + z * tk.by + y] = xn;
         if (x == tk.bx - 1 && fslot[1] >= 0)

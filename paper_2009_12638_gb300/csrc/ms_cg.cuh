@@ -50,30 +50,80 @@ __device__ __forceinline__ Slab make_slab(int bx, int by, int bz, unsigned rank,
   return s;
 }
 
-// Shared memory used by the reductions of one cluster.
-struct RedSmem {
-  double slots[3][2][kMaxCluster];  // [phase][value][cta]: residual pair, eta, gamma
-  double wsum[2][32];
-};
+// Scale applied to the residual before it is rounded to the inner precision:
+// for FP32 a power of two (exact) close to 1/||bhat||, so the inner solve
+// works on O(relative residual) numbers whatever the magnitude of the data;
+// FP64 needs none.
+template <typename T>
+__device__ __forceinline__ double inner_scale(double inv_bnorm) {
+  if (sizeof(T) == sizeof(double) || !(inv_bnorm > 0.0) || !isfinite(inv_bnorm)) return 1.0;
+  int e;
+  frexp(inv_bnorm, &e);
+  return ldexp(1.0, e - 1);
+}
+
+template <typename T>
+__device__ __forceinline__ T step_alpha(const RedSmem& sm);
+template <>
+__device__ __forceinline__ float step_alpha<float>(const RedSmem& sm) { return sm.alpha; }
+template <>
+__device__ __forceinline__ double step_alpha<double>(const RedSmem& sm) { return sm.alpha_d; }
+template <typename T>
+__device__ __forceinline__ T step_beta(const RedSmem& sm);
+template <>
+__device__ __forceinline__ float step_beta<float>(const RedSmem& sm) { return sm.beta; }
+template <>
+__device__ __forceinline__ double step_beta<double>(const RedSmem& sm) { return sm.beta_d; }
+
+// CG scalar bookkeeping, run by thread 0 only (see cluster_reduce).
+__device__ __forceinline__ void cg_begin(RedSmem& sm, double gamma0, double inner_rtol, int inner_maxit) {
+  if (threadIdx.x == 0) {
+    sm.gamma = gamma0;
+    sm.gamma0 = gamma0;
+    sm.stop = inner_rtol * sqrt(gamma0);
+    sm.m = 0;
+    sm.done = (!(gamma0 > 0.0) || inner_maxit <= 0) ? 1 : 0;
+    sm.beta = 0.f;
+    sm.beta_d = 0.0;
+  }
+  __syncthreads();
+}
+// after eta = p.q: curvature breakdown (or NaN) ends the solve, else alpha = gamma / eta
+__device__ __forceinline__ void cg_after_eta(RedSmem& sm, double eta) {
+  if (!(eta > 0.0)) {
+    sm.done = 1;
+  } else {
+    sm.alpha_d = sm.gamma / eta;
+    sm.alpha = (float)sm.alpha_d;
+  }
+}
+// after gamma_new = r.r: count the step, stop test ||r|| <= rtol ||r0||, else beta
+__device__ __forceinline__ void cg_after_gamma(RedSmem& sm, double gnew, int inner_maxit) {
+  sm.m += 1;
+  if (sqrt(gnew) <= sm.stop || sm.m >= inner_maxit) {
+    sm.done = 1;
+  } else {
+    sm.beta_d = gnew / sm.gamma;
+    sm.beta = (float)sm.beta_d;
+    sm.gamma = gnew;
+  }
+}
 
 // Runs CG from d = 0 on r (gamma0 = r.r already reduced).  Returns the
 // number of iterations m; d holds the correction when m > 0.
 template <typename T, int NT>
 __device__ int block_cg(const CgVecs<T>& v, const Slab& sl, double gamma0, double inner_rtol, int inner_maxit,
                         RedSmem& sm, unsigned rank, unsigned csize) {
-  if (!(gamma0 > 0.0)) return 0;
+  cg_begin(sm, gamma0, inner_rtol, inner_maxit);
+  if (sm.done) return 0;
   const int tid = threadIdx.x;
   const int plane = sl.plane, bx = sl.bx, by = sl.by, bz = sl.bz, z0 = sl.z0, z1 = sl.z1;
-  double gamma = gamma0;
-  const double stop = inner_rtol * sqrt(gamma0);
-  double beta = 0.0;
-  int m = 0;
   T* po = v.p0;
   T* pn = v.p1;
   T* const rv = v.r;  // written by pass B, read by pass A: plain coherent loads
-  while (m < inner_maxit) {
-    const bool first = (m == 0);
-    const T bT = (T)beta;
+  bool first = true;
+  for (;;) {
+    const T bT = step_beta<T>(sm);
     // ---------------- pass A
     T eta_loc = 0;
     for (int c = tid; c < plane; c += NT) {
@@ -98,12 +148,13 @@ __device__ int block_cg(const CgVecs<T>& v, const Slab& sl, double gamma0, doubl
       }
 #undef MS_PVAL
     }
-    double red1[1] = {(double)eta_loc};
-    cluster_sum<NT, 1>(red1, sm.slots[1], sm.wsum, rank, csize);
-    const double eta = red1[0];
-    if (!(eta > 0.0)) break;  // curvature breakdown (or NaN): keep d from earlier steps
-    const double alpha = gamma / eta;
-    const T aT = (T)alpha;
+    {
+      const T red1[1] = {eta_loc};
+      cluster_reduce<NT, 1>(red1, sm.slots[1], sm.wsum, rank, csize,
+                            [&](double (&t)[1]) { cg_after_eta(sm, t[0]); });
+    }
+    if (sm.done) break;
+    const T aT = step_alpha<T>(sm);
     // ---------------- pass B
     T g_loc = 0;
     for (int c = tid; c < plane; c += NT) {
@@ -128,18 +179,18 @@ __device__ int block_cg(const CgVecs<T>& v, const Slab& sl, double gamma0, doubl
         pc = pzp;
       }
     }
-    double red2[1] = {(double)g_loc};
-    cluster_sum<NT, 1>(red2, sm.slots[2], sm.wsum, rank, csize);
-    const double gnew = red2[0];
-    m += 1;
-    if (sqrt(gnew) <= stop) break;
-    beta = gnew / gamma;
-    gamma = gnew;
+    {
+      const T red2[1] = {g_loc};
+      cluster_reduce<NT, 1>(red2, sm.slots[2], sm.wsum, rank, csize,
+                            [&](double (&t)[1]) { cg_after_gamma(sm, t[0], inner_maxit); });
+    }
+    if (sm.done) break;
+    first = false;
     T* t = po;
     po = pn;
     pn = t;
   }
-  return m;
+  return sm.m;
 }
 
 }  // namespace ms

@@ -56,20 +56,26 @@ __device__ __forceinline__ double warp_sum_to_lane0(double v) {
   return v;
 }
 
-// Deterministic cluster-wide sum of NV doubles per thread.  Every CTA ends
-// with bit-identical totals: each CTA's partial is formed once (lane 0 of
-// warp 0), stored into slot[rank] of every CTA, and every CTA adds the slots
-// in rank order.  `slots` is [NV][kMaxCluster] shared doubles that must not
-// be reused by another reduction before the next cluster barrier; `wsum` is
-// [NV][32] shared doubles.  Contains one cluster barrier.
-template <int NT, int NV>
-__device__ __forceinline__ void cluster_sum(double (&v)[NV], double (*slots)[kMaxCluster], double (*wsum)[32],
-                                            unsigned rank, unsigned csize) {
+// Deterministic cluster-wide sum of NV values per thread (TA = float or
+// double accumulators).  Every CTA ends with bit-identical totals: warps sum
+// in TA, warp 0 sums the warp totals in FP64, each CTA's total is stored into
+// slot[rank] of every CTA (DSMEM), and after the cluster barrier warp 0 of
+// every CTA adds the slots in the same tree order.  `finish(tot)` then runs
+// on thread 0 alone (FP64 scalar work -- divisions, square roots -- is slow
+// on this GPU, so it is never replicated across threads) and may write
+// shared memory that every thread reads after this function returns.
+// `slots` must not be reused by another reduction before the next cluster
+// barrier.  Contains one cluster barrier and two CTA barriers.
+template <int NT, int NV, typename TA, typename F>
+__device__ __forceinline__ void cluster_reduce(const TA (&v)[NV], double (*slots)[16], double (*wsum)[32],
+                                               unsigned rank, unsigned csize, F&& finish) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int a = 0; a < NV; ++a) {
-    double w = warp_sum_to_lane0(v[a]);
-    if (lane == 0) wsum[a][warp] = w;
+    TA w = v[a];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
+    if (lane == 0) wsum[a][warp] = (double)w;
   }
   __syncthreads();
   if (warp == 0) {
@@ -82,13 +88,29 @@ __device__ __forceinline__ void cluster_sum(double (&v)[NV], double (*slots)[kMa
     }
   }
   cl_barrier();
+  if (warp == 0) {
+    double tot[NV];
 #pragma unroll
-  for (int a = 0; a < NV; ++a) {
-    double s = 0.0;
-    for (unsigned i = 0; i < csize; ++i) s += slots[a][i];
-    v[a] = s;
+    for (int a = 0; a < NV; ++a) {
+      double w = (lane < (int)csize) ? slots[a][lane] : 0.0;
+      tot[a] = warp_sum_to_lane0(w);
+    }
+    if (lane == 0) finish(tot);
   }
+  __syncthreads();
 }
+
+// Shared memory used by the reductions of one cluster, and the CG scalars
+// that thread 0 derives from them and every thread reads.
+struct RedSmem {
+  double slots[3][2][kMaxCluster];  // [phase][value][cta]: residual pair, eta, gamma
+  double wsum[2][32];
+  double tot[2];                    // totals of the last reduction
+  double gamma, gamma0, stop;       // CG state (thread 0 writes)
+  float alpha, beta;                // CG step scalars in the inner precision
+  double alpha_d, beta_d;           // the same in FP64 (FP64 inner path)
+  int m, done;                      // iterations taken, loop exit flag
+};
 
 // Neighbour sums of interior grid point (gx, gy, gz) of one rhs: `inner`
 // gets the neighbours inside the grid, `outer` the Dirichlet values of the

@@ -51,6 +51,7 @@ struct SweepArgs {
   int outer_maxit;
   const int* k_dev;
   unsigned long long* inner_count;  // [nrhs][2]: inner iterations, inner lattice updates
+  const double* inv_bnorm;          // [nrhs] 1/||bhat|| (1 if bhat = 0): FP32 inner scaling
   int* err;
 };
 
@@ -127,5 +128,11 @@ cudaError_t launch_resid(const ResidArgs& a, double* out /*[nrhs][2]*/, double* 
 cudaError_t launch_face_gather(const Geo& g, const double* lam, double* grad, cudaStream_t s);
 cudaError_t launch_async_init(const AsyncArgs& a, cudaStream_t s);
 cudaError_t launch_async_rearm(const AsyncArgs& a, cudaStream_t s);
+// on-chip (resident) FP32 inner CG, sync mode (ms_resident.cu)
+int res_variant_count();
+void res_variant_info(int v, int* nt, int* kc, int* zs);
+cudaError_t res_max_clusters(int variant, int cluster, size_t smem_bytes, int* out);
+cudaError_t launch_res_sweep(int variant, int cluster, int slots, size_t smem_bytes, const SweepArgs& a,
+                             cudaStream_t s);
 
 }  // namespace ms

@@ -63,7 +63,8 @@ __global__ void __launch_bounds__(NT, 1) sweep_kernel(const SweepArgs a) {
     const double* __restrict__ xr = xin + rb;
     const double* __restrict__ fr = a.f ? a.f + rb : nullptr;
     const double* __restrict__ br = a.bnd ? a.bnd + (long long)tk.rhs * g.nbnd : nullptr;
-    // ---- 1. block residual in FP64, stored as T
+    // ---- 1. block residual in FP64, stored as T (FP32: times a power of two ~ 1/||bhat||, undone in 3.)
+    const double scale = inner_scale<T>(a.inv_bnorm[tk.rhs]), unscale = 1.0 / scale;
     double red0[2] = {0.0, 0.0};
     {
       double s_loc = 0.0;
@@ -78,7 +79,7 @@ __global__ void __launch_bounds__(NT, 1) sweep_kernel(const SweepArgs a) {
           const double bh = fr ? fr[gi] + so : so;
           const double rr = bh - (6.0 * xr[gi] - si);
           s_loc += rr * rr;
-          const T rt = (T)rr;
+          const T rt = (T)(rr * scale);
           v.r[z * sl.plane + c] = rt;
           g_loc += rt * rt;
         }
@@ -86,7 +87,12 @@ __global__ void __launch_bounds__(NT, 1) sweep_kernel(const SweepArgs a) {
       red0[0] = s_loc;
       red0[1] = (double)g_loc;
     }
-    cluster_sum<NT, 2>(red0, sm.slots[0], sm.wsum, rank, csize);
+    cluster_reduce<NT, 2>(red0, sm.slots[0], sm.wsum, rank, csize, [&](double (&t)[2]) {
+      sm.tot[0] = t[0];
+      sm.tot[1] = t[1];
+    });
+    red0[0] = sm.tot[0];
+    red0[1] = sm.tot[1];
     if (rank == 0 && tid == 0) a.partial[t] = red0[0];
     if (residual_only) continue;
     // ---- 2. inner CG
@@ -97,7 +103,7 @@ __global__ void __launch_bounds__(NT, 1) sweep_kernel(const SweepArgs a) {
       const int gx = tk.ox + c % tk.bx, gy = tk.oy + c / tk.bx;
       for (int z = sl.z0; z < sl.z1; ++z) {
         const long long gi = (long long)(tk.oz + z) * nxy + (long long)gy * g.nx + gx;
-        xo[gi] = (m > 0) ? xr[gi] + (double)v.d[z * sl.plane + c] : xr[gi];
+        xo[gi] = (m > 0) ? xr[gi] + (double)v.d[z * sl.plane + c] * unscale : xr[gi];
       }
     }
     if (rank == 0 && tid == 0 && m > 0) {

@@ -1,0 +1,254 @@
+// ms_resident.cu -- synchronous outer sweep with the on-chip inner CG
+// (ms_resident.cuh), FP32 inner / FP64 outer.  Same contract as
+// sweep_kernel in ms_kernels.cu (one launch per sweep, dynamic task queue,
+// x double buffered, block partials for the check kernel), but the CG state
+// of the block being solved never leaves the cluster: the residual phase
+// writes r straight into registers, and the update reads d from registers.
+#include <cuda_runtime.h>
+
+#include "ms_device.cuh"
+#include "ms_internal.h"
+#include "ms_resident.cuh"
+
+namespace ms {
+
+// Residual r = bhat - A x^k on this CTA's strips (FP64), multiplied by the
+// power-of-two `scale` (~1/||bhat||, exact) and rounded into r4, so that the
+// FP32 inner solve sees O(relative residual) values whatever the problem's
+// magnitude; the boundary planes of r are pushed to the neighbour CTAs'
+// r-halo planes.  s64: FP64 sum of squares of the unscaled r; g32: FP32 sum
+// of squares of the scaled, rounded r.
+template <int NT, int KC, int ZS>
+__device__ __forceinline__ void resident_residual(float4 (&r4)[KC][ZS], const ResGeo& g, const Strips<KC>& s,
+                                                  const Task& tk, const Geo& G, const double* __restrict__ xr,
+                                                  const double* __restrict__ fr, const double* __restrict__ br,
+                                                  double scale, float* sp, unsigned rank, unsigned csize,
+                                                  double& s64, float& g32) {
+  float* rh_lo = sp + (long long)(ZS + 2) * g.ps;
+  float* rh_hi = rh_lo + g.ps;
+  const long long nxy = (long long)G.nx * G.ny;
+  double sl = 0.0;
+  float gl = 0.f;
+#pragma unroll
+  for (int k = 0; k < KC; ++k) {
+    const int y = s.st[k] >= 0 ? s.st[k] / g.spr : 0;
+    const int gx0 = tk.ox + 4 * (s.st[k] >= 0 ? s.st[k] - y * g.spr : 0), gy = tk.oy + y;
+#pragma unroll
+    for (int z = 0; z < ZS; ++z) {
+      float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (s.msk[k] && z < g.nzs) {
+        const int gz = tk.oz + g.z0 + z;
+        float rv[4];
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          rv[l] = 0.f;
+          if (s.msk[k] & (1u << l)) {
+            const int gx = gx0 + l;
+            const long long gi = (long long)gz * nxy + (long long)gy * G.nx + gx;
+            double si, so;
+            nbr_sums(G, xr, br, gx, gy, gz, gi, si, so);
+            const double bh = fr ? fr[gi] + so : so;
+            const double rr = bh - (6.0 * xr[gi] - si);
+            sl += rr * rr;
+            rv[l] = (float)(rr * scale);
+          }
+        }
+        r = make_float4(rv[0], rv[1], rv[2], rv[3]);
+        gl += dot4(r, r);
+        if (z == 0 && rank > 0) st_cluster_v4(rh_hi + s.off[k], rank - 1, r);
+        if (z == g.nzs - 1 && rank + 1 < csize) st_cluster_v4(rh_lo + s.off[k], rank + 1, r);
+      }
+      r4[k][z] = r;
+    }
+  }
+  s64 = sl;
+  g32 = gl;
+}
+
+// power of two closest (within a factor 2) to v > 0, 1 otherwise
+__device__ __forceinline__ double pow2_near(double v) {
+  if (!(v > 0.0) || !isfinite(v)) return 1.0;
+  int e;
+  frexp(v, &e);
+  return ldexp(1.0, e - 1);
+}
+
+template <int NT>
+__device__ __forceinline__ void zero_smem(float4* p, int n4) {
+  for (int i = threadIdx.x; i < n4; i += NT) p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+template <int NT, int KC, int ZS>
+__global__ void __launch_bounds__(NT, 1) res_sweep_kernel(const SweepArgs a, int smem_f4) {
+  extern __shared__ float4 dyn4[];
+  float* sp = reinterpret_cast<float*>(dyn4);
+  __shared__ RedSmem red;
+  __shared__ ResRed rred;
+  __shared__ int s_task[2];
+  if (*a.all_done) return;
+  const unsigned rank = cl_rank(), csize = cl_size();
+  const int tid = threadIdx.x;
+  const int k = *a.k_dev;
+  const double* __restrict__ xin = (k & 1) ? a.xbuf1 : a.xbuf0;
+  double* __restrict__ xout = (k & 1) ? a.xbuf0 : a.xbuf1;
+  const bool residual_only = (k >= a.outer_maxit);
+  const Geo G = a.g;
+  const long long nxy = (long long)G.nx * G.ny;
+  zero_smem<NT>(dyn4, smem_f4);
+  int par = 0;
+  for (;;) {
+    if (rank == 0 && tid == 0) {
+      const int t = (int)atomicAdd(a.counter, 1u);
+      for (unsigned j = 0; j < csize; ++j) cl_store(&s_task[par], j, t);
+    }
+    cl_barrier();
+    const int t = s_task[par];
+    par ^= 1;
+    if (t >= a.ntasks) break;
+    const Task tk = a.tasks[t];
+    if (a.rhs_state[tk.rhs] != kActive) continue;
+    // capacity check, identical in every CTA of the cluster
+    {
+      const int spr = (tk.bx + 3) >> 2;
+      const int nzs_max = (tk.bz + (int)csize - 1) / (int)csize;
+      if (tk.bz < (int)csize || nzs_max > ZS || spr * tk.by > KC * NT ||
+          res_smem_floats(tk.bx, tk.by, ZS) > 4LL * smem_f4) {
+        if (tid == 0) atomicOr(a.err, kErrGeometry);
+        continue;
+      }
+    }
+    const ResGeo g = make_res_geo(tk.bx, tk.by, tk.bz, rank, csize);
+    const Strips<KC> s = make_strips<NT, KC>(g);
+    const double scale = pow2_near(a.inv_bnorm[tk.rhs]), unscale = 1.0 / scale;
+    const long long rb = (long long)tk.rhs * G.npts;
+    const double* __restrict__ xr = xin + rb;
+    const double* __restrict__ fr = a.f ? a.f + rb : nullptr;
+    const double* __restrict__ br = a.bnd ? a.bnd + (long long)tk.rhs * G.nbnd : nullptr;
+    float4 r4[KC][ZS], d4[KC][ZS];
+    double red0[2];
+    {
+      double s64;
+      float g32;
+      resident_residual<NT, KC, ZS>(r4, g, s, tk, G, xr, fr, br, scale, sp, rank, csize, s64, g32);
+      red0[0] = s64;
+      red0[1] = (double)g32;
+    }
+    cluster_reduce<NT, 2>(red0, red.slots[0], red.wsum, rank, csize, [&](double (&t)[2]) {
+      red.tot[0] = t[0];
+      red.tot[1] = t[1];
+    });
+    red0[0] = red.tot[0];
+    red0[1] = red.tot[1];
+    if (rank == 0 && tid == 0) a.partial[t] = red0[0];
+    int m = 0;
+    if (!residual_only)
+      m = resident_cg<NT, KC, ZS>(r4, d4, g, s, sp, (float)red0[1], (float)a.inner_rtol, a.inner_maxit, rred, rank,
+                                  csize);
+    // every cluster barrier of this task is behind us: the smem can be cleared for the next one
+    zero_smem<NT>(dyn4, smem_f4);
+    if (residual_only) continue;
+    double* __restrict__ xo = xout + rb;
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk) {
+      if (!s.msk[kk]) continue;
+      const int y = s.st[kk] / g.spr;
+      const long long row = (long long)(tk.oy + y) * G.nx + tk.ox + 4 * (s.st[kk] - y * g.spr);
+#pragma unroll
+      for (int z = 0; z < ZS; ++z) {
+        if (z >= g.nzs) continue;
+        const long long gi0 = (long long)(tk.oz + g.z0 + z) * nxy + row;
+        const float4 d = d4[kk][z];
+        const float dv[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          if (!(s.msk[kk] & (1u << l))) continue;
+          xo[gi0 + l] = (m > 0) ? xr[gi0 + l] + (double)dv[l] * unscale : xr[gi0 + l];
+        }
+      }
+    }
+    if (rank == 0 && tid == 0 && m > 0) {
+      atomicAdd(a.inner_count + 2 * tk.rhs, (unsigned long long)m);
+      atomicAdd(a.inner_count + 2 * tk.rhs + 1, (unsigned long long)m * (unsigned long long)tk.bx * tk.by * tk.bz);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- variants
+// (NT threads, KC strips per thread, ZS planes per CTA at most)
+struct ResVariant {
+  int nt, kc, zs;
+};
+static const ResVariant kResVariants[] = {{512, 2, 4}, {512, 1, 8}, {256, 2, 4}, {256, 1, 8}, {512, 4, 2}};
+constexpr int kNumResVariants = sizeof(kResVariants) / sizeof(kResVariants[0]);
+
+template <int NT, int KC, int ZS>
+static cudaError_t prep_res(int cluster, size_t smem_bytes, void** fn) {
+  auto kern = res_sweep_kernel<NT, KC, ZS>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+  if (e != cudaSuccess) return e;
+  if (cluster > 8) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  *fn = (void*)kern;
+  return cudaSuccess;
+}
+
+static cudaError_t res_fn(int variant, int cluster, size_t smem_bytes, void** fn) {
+  switch (variant) {
+    case 0: return prep_res<512, 2, 4>(cluster, smem_bytes, fn);
+    case 1: return prep_res<512, 1, 8>(cluster, smem_bytes, fn);
+    case 2: return prep_res<256, 2, 4>(cluster, smem_bytes, fn);
+    case 3: return prep_res<256, 1, 8>(cluster, smem_bytes, fn);
+    case 4: return prep_res<512, 4, 2>(cluster, smem_bytes, fn);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int res_variant_count() { return kNumResVariants; }
+
+void res_variant_info(int v, int* nt, int* kc, int* zs) {
+  *nt = kResVariants[v].nt;
+  *kc = kResVariants[v].kc;
+  *zs = kResVariants[v].zs;
+}
+
+static void res_cfg(cudaLaunchConfig_t* cfg, cudaLaunchAttribute* at, int nt, int cluster, int slots, size_t smem,
+                    cudaStream_t s) {
+  *cfg = cudaLaunchConfig_t{};
+  cfg->gridDim = dim3((unsigned)(cluster * slots), 1, 1);
+  cfg->blockDim = dim3((unsigned)nt, 1, 1);
+  cfg->dynamicSmemBytes = smem;
+  cfg->stream = s;
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)cluster;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg->attrs = at;
+  cfg->numAttrs = 1;
+}
+
+cudaError_t res_max_clusters(int variant, int cluster, size_t smem_bytes, int* out) {
+  void* fn = nullptr;
+  cudaError_t e = res_fn(variant, cluster, smem_bytes, &fn);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute at[1];
+  res_cfg(&cfg, at, kResVariants[variant].nt, cluster, 64, smem_bytes, nullptr);
+  return cudaOccupancyMaxActiveClusters(out, fn, &cfg);
+}
+
+cudaError_t launch_res_sweep(int variant, int cluster, int slots, size_t smem_bytes, const SweepArgs& a,
+                             cudaStream_t s) {
+  void* fn = nullptr;
+  cudaError_t e = res_fn(variant, cluster, smem_bytes, &fn);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute at[1];
+  res_cfg(&cfg, at, kResVariants[variant].nt, cluster, slots, smem_bytes, s);
+  const int smem_f4 = (int)(smem_bytes / 16);
+  void* args[] = {(void*)&a, (void*)&smem_f4};
+  return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+}  // namespace ms

@@ -1,0 +1,275 @@
+// ms_resident.cuh -- the inner CG (sections 2.2 and 3 of the paper) with the
+// whole block state on chip: one thread-block cluster per block, no global
+// memory traffic inside the inner loop.
+//
+// Layout.  The block (bx*by*bz, FP32) is cut into z-slabs, one per CTA
+// (every CTA owns >= 1 plane).  A thread owns KC "strips" -- 4 consecutive x
+// points of one (y) row -- in every plane of its slab (<= ZS planes), and
+// keeps r and d of those points in registers as float4.  p lives in shared
+// memory as nzs+2 planes (own planes plus one halo plane below and above),
+// each with a zero row above/below and zero columns left/right, so the
+// stencil needs no branches: zero padding is the block's Dirichlet-0 face
+// (A_ii is A restricted to the block).
+//
+// Halo planes without a third barrier.  p_new = r + beta p_old needs the
+// neighbour CTA's r; after pass B each CTA pushes its first/last plane of r
+// into its neighbours' r-halo planes (DSMEM stores, made visible by the
+// gamma reduction's cluster barrier).  Every CTA then forms p_new on its own
+// planes AND on its halo planes with the same fused multiply-add the owner
+// uses, so the copies agree bit for bit.
+//
+// Per CG iteration: pass A (stencil from shared memory, eta = p.q), cluster
+// sum, pass B (stencil again, d += alpha p, r -= alpha q, gamma = r.r, r
+// halo push), cluster sum, pass C (p = r + beta p on own and halo planes).
+#pragma once
+#include "ms_cg.cuh"
+#include "ms_device.cuh"
+
+namespace ms {
+
+struct ResGeo {
+  int bx, by, bz;
+  int spr;      // strips per row = ceil(bx / 4)
+  int nstrips;  // spr * by
+  int rp;       // smem row pitch in floats: 4 + 4*spr + 4
+  int ps;       // smem plane stride in floats: (by + 2) * rp
+  int z0, nzs;  // own planes
+};
+
+__device__ __forceinline__ ResGeo make_res_geo(int bx, int by, int bz, unsigned rank, unsigned csize) {
+  ResGeo g;
+  g.bx = bx;
+  g.by = by;
+  g.bz = bz;
+  g.spr = (bx + 3) >> 2;
+  g.nstrips = g.spr * by;
+  g.rp = 4 * g.spr + 8;
+  g.ps = (by + 2) * g.rp;
+  g.z0 = (int)(((long long)bz * rank) / csize);
+  g.nzs = (int)(((long long)bz * (rank + 1)) / csize) - g.z0;
+  return g;
+}
+
+// floats of dynamic shared memory for a geometry: p (nzs_max + 2 planes) and 2 r-halo planes
+__host__ __device__ inline long long res_smem_floats(int bx, int by, int nzs_max) {
+  const long long rp = 4 * ((bx + 3) / 4) + 8;
+  const long long ps = (by + 2) * rp;
+  return (nzs_max + 4) * ps;
+}
+
+__device__ __forceinline__ void st_cluster_v4(float* local, unsigned rank, float4 v) {
+  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(cl_map(local, rank)), "f"(v.x), "f"(v.y),
+               "f"(v.z), "f"(v.w)
+               : "memory");
+}
+
+__device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void sts4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+
+__device__ __forceinline__ float4 mask4(float4 v, unsigned m) {
+  return make_float4((m & 1u) ? v.x : 0.f, (m & 2u) ? v.y : 0.f, (m & 4u) ? v.z : 0.f, (m & 8u) ? v.w : 0.f);
+}
+
+__device__ __forceinline__ float dot4(float4 a, float4 b) { return (a.x * b.x + a.y * b.y) + (a.z * b.z + a.w * b.w); }
+
+__device__ __forceinline__ void st_cluster_f32(float* local, unsigned rank, float v) {
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(cl_map(local, rank)), "f"(v) : "memory");
+}
+
+// Cluster-wide FP32 sum.  Each warp stores its total into slot[rank][warp] of
+// every CTA; after the single cluster barrier EVERY warp of every CTA adds
+// all slots in the same order, so every thread holds the bit-identical total
+// and no CTA-wide barrier or broadcast is needed.  `slots` must not be
+// reused by another reduction before the next cluster barrier.
+template <int NT>
+__device__ __forceinline__ float cluster_sum_f32(float v, float* slots, unsigned rank, unsigned csize) {
+  constexpr int NW = NT / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  v = __shfl_sync(0xffffffffu, v, 0);
+  if (lane < (int)csize) st_cluster_f32(&slots[rank * NW + warp], (unsigned)lane, v);
+  cl_barrier();
+  float acc = 0.f;
+  const int n = (int)csize * NW;
+  for (int i = lane; i < n; i += 32) acc += slots[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  return __shfl_sync(0xffffffffu, acc, 0);
+}
+
+// 7-point stencil q = 6p - sum(nbrs) on the 4 points of a strip.  y and z
+// neighbours come from shared memory / registers; the x neighbours at the
+// strip ends come from the adjacent lanes (which hold the adjacent strips of
+// the same row) by warp shuffle, or from shared memory (zero padding at a
+// row end) for the first and last lane.  All 32 lanes must call it.
+__device__ __forceinline__ float4 stencil4(const float* c_ptr, int rp, float4 c, float4 zm, float4 zp,
+                                           bool left_lane, bool right_lane) {
+  const float4 ym = lds4(c_ptr - rp);
+  const float4 yp = lds4(c_ptr + rp);
+  const float xl_s = __shfl_up_sync(0xffffffffu, c.w, 1);
+  const float xr_s = __shfl_down_sync(0xffffffffu, c.x, 1);
+  const float xl = left_lane ? xl_s : c_ptr[-1];
+  const float xr = right_lane ? xr_s : c_ptr[4];
+  float4 q;
+  q.x = 6.f * c.x - (((xl + c.y) + (ym.x + yp.x)) + (zm.x + zp.x));
+  q.y = 6.f * c.y - (((c.x + c.z) + (ym.y + yp.y)) + (zm.y + zp.y));
+  q.z = 6.f * c.z - (((c.y + c.w) + (ym.z + yp.z)) + (zm.z + zp.z));
+  q.w = 6.f * c.w - (((c.z + xr) + (ym.w + yp.w)) + (zm.w + zp.w));
+  return q;
+}
+
+// Per-thread strip bookkeeping for one task.  Threads without a strip keep
+// off = 0 (a harmless in-bounds smem address) and msk = 0: they run every
+// loop (shuffles need all lanes) but store nothing.
+template <int KC>
+struct Strips {
+  int off[KC];       // smem offset (floats) of the strip in plane 0 (the lower halo plane)
+  unsigned msk[KC];  // lanes with x < bx (0 = no strip)
+  unsigned nb[KC];   // bit 0: left strip is held by lane-1; bit 1: right strip by lane+1
+  int st[KC];        // strip id (row-major over the plane), -1 if none
+};
+
+template <int NT, int KC>
+__device__ __forceinline__ Strips<KC> make_strips(const ResGeo& g) {
+  Strips<KC> s;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < KC; ++k) {
+    const int st = threadIdx.x + k * NT;
+    if (st < g.nstrips) {
+      const int y = st / g.spr, xs = st - y * g.spr;
+      s.off[k] = (y + 1) * g.rp + 4 + 4 * xs;
+      const int rem = g.bx - 4 * xs;
+      s.msk[k] = rem >= 4 ? 0xFu : ((1u << rem) - 1u);
+      s.nb[k] = ((lane > 0 && xs > 0) ? 1u : 0u) | ((lane < 31 && xs + 1 < g.spr) ? 2u : 0u);
+      s.st[k] = st;
+    } else {
+      s.off[k] = 0;
+      s.msk[k] = 0u;
+      s.nb[k] = 0u;
+      s.st[k] = -1;
+    }
+  }
+  return s;
+}
+
+// Reduction slots of the resident engine (FP32, one per warp per CTA).
+struct ResRed {
+  float eta[kMaxCluster * 32];
+  float gam[kMaxCluster * 32];
+};
+
+// Inner CG on the resident state.  On entry r4 holds r (padding lanes 0),
+// the r-halo planes hold the neighbours' boundary r (pushed before the
+// cluster barrier of the residual reduction), p planes are zero.  Returns
+// m; d4 holds the correction when m > 0.  Scalars are FP32 and computed
+// identically by every thread of the cluster.
+template <int NT, int KC, int ZS>
+__device__ int resident_cg(float4 (&r4)[KC][ZS], float4 (&d4)[KC][ZS], const ResGeo& g, const Strips<KC>& s,
+                           float* sp, float gamma0, float inner_rtol, int inner_maxit, ResRed& rr, unsigned rank,
+                           unsigned csize) {
+  float* rh_lo = sp + (long long)(ZS + 2) * g.ps;  // neighbour below's top plane of r
+  float* rh_hi = rh_lo + g.ps;                     // neighbour above's bottom plane of r
+  float* p_lo = sp;                                // p halo plane below (plane 0)
+  float* p_hi = sp + (long long)(g.nzs + 1) * g.ps;
+  const bool has_lo = rank > 0, has_hi = rank + 1 < csize;
+  const int tid = threadIdx.x;
+  if (!(gamma0 > 0.f) || inner_maxit <= 0) return 0;
+  const float stop = inner_rtol * sqrtf(gamma0);
+  float gamma = gamma0, beta = 0.f;
+  int m = 0;
+  for (;;) {
+    // ---------------- pass C: p = r + beta p on own planes and both halo planes
+    // (beta = 0 on entry: p = r, halo p = neighbours' r; p planes start zeroed)
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+      if (!s.msk[k]) continue;
+#pragma unroll
+      for (int z = 0; z < ZS; ++z) {
+        if (z >= g.nzs) break;
+        float* pp = sp + (long long)(z + 1) * g.ps + s.off[k];
+        const float4 po = lds4(pp);
+        const float4 r = r4[k][z];
+        sts4(pp, make_float4(fmaf(beta, po.x, r.x), fmaf(beta, po.y, r.y), fmaf(beta, po.z, r.z),
+                             fmaf(beta, po.w, r.w)));
+      }
+    }
+    for (int st = tid; st < g.nstrips; st += NT) {
+      const int y = st / g.spr, xs = st - y * g.spr;
+      const int o = (y + 1) * g.rp + 4 + 4 * xs;
+      if (has_lo) {
+        const float4 po = lds4(p_lo + o), r = lds4(rh_lo + o);
+        sts4(p_lo + o, make_float4(fmaf(beta, po.x, r.x), fmaf(beta, po.y, r.y), fmaf(beta, po.z, r.z),
+                                   fmaf(beta, po.w, r.w)));
+      }
+      if (has_hi) {
+        const float4 po = lds4(p_hi + o), r = lds4(rh_hi + o);
+        sts4(p_hi + o, make_float4(fmaf(beta, po.x, r.x), fmaf(beta, po.y, r.y), fmaf(beta, po.z, r.z),
+                                   fmaf(beta, po.w, r.w)));
+      }
+    }
+    __syncthreads();
+    // ---------------- pass A: q = A_ii p, eta = p.q
+    float eta_loc = 0.f;
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+      const float* base = sp + s.off[k];
+      const bool lft = s.nb[k] & 1u, rgt = s.nb[k] & 2u;
+      float4 zm = lds4(base);
+      float4 c = lds4(base + g.ps);
+#pragma unroll
+      for (int z = 0; z < ZS; ++z) {
+        if (z >= g.nzs) break;
+        const float* cp = base + (long long)(z + 1) * g.ps;
+        const float4 zp = lds4(cp + g.ps);
+        const float4 q = mask4(stencil4(cp, g.rp, c, zm, zp, lft, rgt), s.msk[k]);
+        eta_loc += dot4(c, q);
+        zm = c;
+        c = zp;
+      }
+    }
+    const float eta = cluster_sum_f32<NT>(eta_loc, rr.eta, rank, csize);
+    if (!(eta > 0.f)) break;  // curvature breakdown or NaN: keep d from earlier steps
+    const float alpha = gamma / eta;
+    // ---------------- pass B: d += alpha p, r -= alpha q, gamma = r.r, push boundary r
+    float g_loc = 0.f;
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+      const float* base = sp + s.off[k];
+      const bool lft = s.nb[k] & 1u, rgt = s.nb[k] & 2u;
+      float4 zm = lds4(base);
+      float4 c = lds4(base + g.ps);
+#pragma unroll
+      for (int z = 0; z < ZS; ++z) {
+        if (z >= g.nzs) break;
+        const float* cp = base + (long long)(z + 1) * g.ps;
+        const float4 zp = lds4(cp + g.ps);
+        const float4 q = mask4(stencil4(cp, g.rp, c, zm, zp, lft, rgt), s.msk[k]);
+        float4 d = d4[k][z];
+        if (m == 0) d = make_float4(0.f, 0.f, 0.f, 0.f);
+        d4[k][z] = make_float4(fmaf(alpha, c.x, d.x), fmaf(alpha, c.y, d.y), fmaf(alpha, c.z, d.z),
+                               fmaf(alpha, c.w, d.w));
+        float4 r = r4[k][z];
+        r = make_float4(fmaf(-alpha, q.x, r.x), fmaf(-alpha, q.y, r.y), fmaf(-alpha, q.z, r.z),
+                        fmaf(-alpha, q.w, r.w));
+        r4[k][z] = r;
+        g_loc += dot4(r, r);
+        if (s.msk[k]) {
+          if (z == 0 && has_lo) st_cluster_v4(rh_hi + s.off[k], rank - 1, r);
+          if (z == g.nzs - 1 && has_hi) st_cluster_v4(rh_lo + s.off[k], rank + 1, r);
+        }
+        zm = c;
+        c = zp;
+      }
+    }
+    const float gnew = cluster_sum_f32<NT>(g_loc, rr.gam, rank, csize);
+    m += 1;
+    if (sqrtf(gnew) <= stop || m >= inner_maxit) break;
+    beta = gnew / gamma;
+    gamma = gnew;
+  }
+  return m;
+}
+
+}  // namespace ms

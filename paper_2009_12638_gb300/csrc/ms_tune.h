@@ -15,6 +15,8 @@ struct LaunchShape {
   int cluster = 1;
   int threads = 512;
   int slots = 1;
+  int variant = -1;   // >= 0: resident engine variant (ms_resident.cu); -1: streaming engine
+  size_t smem = 0;    // dynamic shared memory bytes (resident engine)
 };
 
 struct Tuner {
@@ -30,7 +32,7 @@ struct Tuner {
 
 // Picks a shape; explicit non-zero requests are honoured.  Returns a
 // cudaError_t value (0 on success).
-int choose_shape(Tuner& t, int prec, int mode, const std::vector<Task>& tasks, long long maxpts, int req_cluster,
-                 int req_threads, int req_slots, LaunchShape* out);
+int choose_shape(Tuner& t, int prec, int mode, int engine, const std::vector<Task>& tasks, long long maxpts,
+                 int req_cluster, int req_threads, int req_slots, LaunchShape* out);
 
 }  // namespace ms

@@ -272,3 +272,80 @@ def test_sync_time_limit_returns_timeout():
     assert st.status == 5
     # the returned iterate is a complete sweep: its true residual is what the stats say
     assert g.residual(x, bnd=cuda(bnd))[0] == pytest.approx(st.rel_residual, rel=1e-12)
+
+
+# ---------------------------------------------------------------- on-chip (resident) engine
+RES_CASES = [
+    (32, 32, 32, [0, 16, 32], [0, 16, 32], [0, 16, 32]),
+    (37, 29, 23, [0, 13, 37], [0, 10, 20, 29], [0, 11, 23]),            # ragged strips and slabs
+    (64, 64, 64, [0, 64], [0, 64], [0, 64]),                             # one 64^3 block
+    (21, 19, 40, [0, 5, 21], [0, 1, 19], [0, 9, 40]),                     # 1-wide rows
+]
+
+
+@pytest.mark.parametrize("case", RES_CASES)
+def test_resident_one_sweep_close_to_oracle(case):
+    """One sweep from x0 = 0 is one FP32 CG solve per block: it must match the
+    FP64 oracle's sweep to FP32-CG accuracy."""
+    nx, ny, nz, cx, cy, cz = case
+    bnd = np.random.default_rng(50).uniform(-1, 1, size=(1, inputs.boundary_size(nx, ny, nz)))
+    g = make_grid(nx, ny, nz, 1, cx, cy, cz)
+    x, st = g.solve(bnd=cuda(bnd), precision="mixed", engine="resident", outer_tol=0.0, outer_maxit=1)
+    ref = oracle.solve(nx, ny, nz, cx, cy, cz, bnd=bnd[0], outer_tol=0.0, outer_maxit=1)
+    assert st.outer_its == 1
+    assert rel_inf(x.cpu().numpy()[0], ref["x"]) <= 2e-4
+    assert st.inner_its == ref["inner_its"] or abs(st.inner_its - ref["inner_its"]) <= 2 * len(cx) * len(cy) * len(cz)
+
+
+@pytest.mark.parametrize("case", RES_CASES)
+def test_resident_converges_like_streaming(case, cluster=0):
+    nx, ny, nz, cx, cy, cz = case
+    bnd = np.random.default_rng(51).uniform(-1, 1, size=(2, inputs.boundary_size(nx, ny, nz)))
+    g = make_grid(nx, ny, nz, 2, cx, cy, cz)
+    xr, sr = g.solve(bnd=cuda(bnd), precision="mixed", engine="resident", cluster=cluster)
+    xs, ss = g.solve(bnd=cuda(bnd), precision="mixed", engine="streaming")
+    assert sr.status == 0 and max(sr.per_rhs_rel) < 1e-8
+    assert (g.residual(xr, bnd=cuda(bnd)) < 1e-8).all()
+    assert abs(sr.outer_its - ss.outer_its) <= max(2, ss.outer_its // 50)
+    ref = oracle.solve(nx, ny, nz, cx, cy, cz, bnd=bnd[1])
+    kappa = 0.5 * (max(nx, ny, nz) + 1) ** 2
+    assert rel_inf(xr.cpu().numpy()[1], ref["x"]) <= 2 * kappa * 1e-8
+
+
+@pytest.mark.parametrize("cluster", [2, 4, 8, 16])
+def test_resident_cluster_sizes(cluster):
+    test_resident_converges_like_streaming(RES_CASES[0], cluster)
+
+
+@pytest.mark.parametrize("magnitude", [1e-30, 1e30])
+@pytest.mark.parametrize("engine", ["resident", "streaming"])
+def test_mixed_is_scale_invariant(magnitude, engine):
+    """The FP32 inner solve works on the residual scaled by a power of two near
+    1/||bhat||, so data of any magnitude converges exactly like O(1) data."""
+    n = 24
+    c = inputs.equal_cuts(n, 2)
+    bnd = np.random.default_rng(53).uniform(-1, 1, size=(1, inputs.boundary_size(n, n, n)))
+    g = make_grid(n, n, n, 1, c, c, c)
+    x1, s1 = g.solve(bnd=cuda(bnd), precision="mixed", engine=engine)
+    xm, sm = g.solve(bnd=cuda(bnd * magnitude), precision="mixed", engine=engine)
+    assert s1.status == 0 and sm.status == 0 and sm.rel_residual < 1e-8
+    assert abs(sm.outer_its - s1.outer_its) <= 1
+    assert rel_inf(xm.cpu().numpy() / magnitude, x1.cpu().numpy()) <= 2 * 0.5 * (n + 1) ** 2 * 1e-8
+
+
+def test_resident_uneven_multi_rhs():
+    cfg = inputs.make_config("batched_uneven", scale=4)
+    g = make_grid(cfg["nx"], cfg["ny"], cfg["nz"], 4, cfg["cx"], cfg["cy"], cfg["cz"])
+    x, st = g.solve(bnd=cuda(cfg["bnd"][:4]), precision="mixed", engine="resident")
+    assert st.status == 0 and max(st.per_rhs_rel) < 1e-8
+
+
+def test_resident_refuses_blocks_that_do_not_fit():
+    g = make_grid(8, 8, 3, 1, [0, 8], [0, 8], [0, 3])  # bz = 3 < any cluster of 4: still fits with c <= 3
+    bnd = np.random.default_rng(52).uniform(-1, 1, size=(1, g.nbnd))
+    x, st = g.solve(bnd=cuda(bnd), precision="mixed", engine="resident")
+    assert st.status == 0
+    big = make_grid(200, 200, 8, 1, [0, 200], [0, 200], [0, 8])  # 50x200 strips per plane: too many
+    with pytest.raises(Exception):
+        big.solve(bnd=torch.zeros(1, big.nbnd, dtype=torch.float64, device="cuda"), precision="mixed",
+                  engine="resident", outer_maxit=1)
