@@ -161,6 +161,36 @@ MS_API int ms_residual(ms_grid* grid, const double* f, const double* bnd, const 
  * device).  lam is [nrhs][nz][ny][nx] (device). */
 MS_API int ms_face_gather(ms_grid* grid, const double* lam, double* grad_bnd, void* stream);
 
+/* The largest nrhs ms_residual_noalloc accepts (its scratch has a fixed size). */
+#define MS_NOALLOC_MAX_RHS 1024
+
+/* ms_residual without any device allocation.  (The paper has no counterpart:
+ * this is an interface for callers, not a step of the method.)
+ *
+ * For callers that cannot call cudaMalloc where they need the residual: code
+ * running while a CUDA graph is captured (an allocation there breaks the
+ * capture), latency-critical loops that cannot absorb cudaMalloc's implicit
+ * device synchronisation, or applications whose device memory is owned by
+ * their own pool allocator.  ms_residual allocates a per-handle workspace on
+ * first use; this function uses instead a fixed 1 MiB array of partial sums
+ * compiled into the library (a static device array that every GPU loading
+ * the library holds until the process exits).
+ *   f, bnd, x: as ms_residual (device; f and bnd may be NULL);
+ *   rel_out:   DEVICE [nrhs] doubles, ||bhat - A x||_2 / ||bhat||_2 per rhs
+ *              (the absolute norm where ||bhat|| = 0), ready on `stream`'s
+ *              timeline when the call returns (no synchronisation).
+ * Limits and caveats:
+ *   - nrhs must be <= MS_NOALLOC_MAX_RHS, else MS_ERR_ARG with a message;
+ *   - the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture on that device;
+ *   - every call on a device shares the one array: calls whose work can
+ *     overlap on the GPU (unordered streams) race on it and must be
+ *     serialised by the caller.  Each call writes all the scratch it reads,
+ *     so no clearing is needed between calls. */
+MS_API int ms_residual_noalloc(ms_grid* grid, const double* f, const double* bnd, const double* x, double* rel_out,
+                               void* stream);
+
 /* Free the handle and its device workspace.  Synchronises the device work
  * the handle issued.  NULL is accepted. */
 MS_API int ms_destroy(ms_grid* grid);

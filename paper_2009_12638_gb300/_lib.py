@@ -25,7 +25,9 @@ PRECISION = {"fp64": 0, "mixed": 1}
 
 # Symbols declared in include/ms.h (checked by the CPU tests).
 EXPORTS = ("ms_boundary_size", "ms_default_opts", "ms_create_grid", "ms_partition", "ms_get_cuts", "ms_solve",
-           "ms_solve_host", "ms_residual", "ms_face_gather", "ms_destroy", "ms_last_error")
+           "ms_solve_host", "ms_residual", "ms_face_gather", "ms_destroy", "ms_last_error",
+           "ms_residual_noalloc")
+NOALLOC_MAX_RHS = 1024
 
 
 class Opts(ctypes.Structure):
@@ -95,11 +97,12 @@ def load(path: str = LIB_PATH):
         lib.ms_solve_host.argtypes = [vp, vp, vp, vp, ctypes.POINTER(Opts), ctypes.POINTER(Stats), vp]
         lib.ms_residual.argtypes = [vp, vp, vp, vp, dp, vp]
         lib.ms_face_gather.argtypes = [vp, vp, vp, vp]
+        lib.ms_residual_noalloc.argtypes = [vp, vp, vp, vp, vp, vp]
         lib.ms_destroy.argtypes = [vp]
         lib.ms_last_error.argtypes = [vp]
         lib.ms_last_error.restype = ctypes.c_char_p
         for name in ("ms_create_grid", "ms_partition", "ms_get_cuts", "ms_solve", "ms_solve_host", "ms_residual",
-                     "ms_face_gather", "ms_destroy"):
+                     "ms_face_gather", "ms_destroy", "ms_residual_noalloc"):
             getattr(lib, name).restype = c_int
         _lib = lib
         return lib

@@ -97,6 +97,20 @@ static int fail(ms_grid* g, int code, const char* fmt, ...) {
   return code;
 }
 
+namespace ms {
+Geo grid_geo(const ms_grid* g) { return g->geo(); }
+int grid_fail(ms_grid* g, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (g) g->err = buf;
+  else g_create_error = buf;
+  return code;
+}
+}  // namespace ms
+
 #define MS_CUDA(g, expr)                                                                        \
   do {                                                                                          \
     cudaError_t e_ = (expr);                                                                    \

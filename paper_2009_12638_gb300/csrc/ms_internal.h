@@ -5,6 +5,8 @@
 
 #include <cstdint>
 
+struct ms_grid;
+
 namespace ms {
 
 constexpr int kMaxCluster = 16;
@@ -116,6 +118,10 @@ struct ResidArgs {
   double* part;  // [nrhs][nblk][2]: sum r^2, sum bhat^2
   int nblk;
 };
+
+// handle accessors for entry points defined outside ms_api.cu
+Geo grid_geo(const ms_grid* g);
+int grid_fail(ms_grid* g, int code, const char* fmt, ...);
 
 // launchers (ms_kernels.cu / ms_async.cu)
 cudaError_t launch_sweep(int prec, int threads, int cluster, int slots, const SweepArgs& a, cudaStream_t s);
