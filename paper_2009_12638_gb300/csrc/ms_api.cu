@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -408,15 +409,45 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
     }
   } evg{ev0, ev1};
 
-  // launch shape
-  LaunchShape shape;
-  int rc = choose_shape(g->tuner, prec, o.mode, o.engine, tasks, maxpts, o.cluster, o.threads, o.slots, &shape);
+  // launch shape: an explicit request, a shape measured earlier for this
+  // problem, or -- sync mode -- candidates measured on the first sweeps
+  std::vector<LaunchShape> all;
+  int rc = list_shapes(g->tuner, prec, o.mode, o.engine, tasks, maxpts, o.cluster, o.threads, o.slots, &all);
   if (rc != 0) return fail(g, MS_ERR_CUDA, "ms_solve: no launchable shape (%s)", cudaGetErrorString((cudaError_t)rc));
+  LaunchShape shape = all.front();
+  std::vector<LaunchShape> cands;
+  const std::vector<long long> sig = signature(prec, o.mode, o.engine, tasks);
+  {
+    auto it = g->tuner.best.find(sig);
+    const bool requested = o.cluster || o.threads || o.slots;
+    if (!requested && it != g->tuner.best.end()) {
+      shape = it->second;
+    } else if (!requested && o.mode == MS_MODE_SYNC) {
+      int nres = 0;
+      bool have_streaming = false;
+      for (const LaunchShape& c : all) {
+        if (c.variant >= 0 && nres < 5) {
+          cands.push_back(c);
+          ++nres;
+        } else if (c.variant < 0 && (!have_streaming || prec == 0)) {
+          cands.push_back(c);
+          have_streaming = true;
+        }
+      }
+      // sweep 0 (heuristic shape) + one sweep per candidate must fit in the sweep budget
+      if (cands.size() < 2 || (long long)o.outer_maxit < 2 * (long long)cands.size()) cands.clear();
+    }
+  }
 
   // workspace
   const long long vec_stride = (maxpts + 31) / 32 * 32;
   CtlLayout L = ctl_layout(g->nrhs);
-  if (shape.variant < 0) MS_CUDA(g, g->scratch.reserve((size_t)shape.slots * 4 * vec_stride * esz));
+  {
+    int streaming_slots = shape.variant < 0 ? shape.slots : 0;
+    for (const LaunchShape& c : cands)
+      if (c.variant < 0) streaming_slots = std::max(streaming_slots, c.slots);
+    if (streaming_slots > 0) MS_CUDA(g, g->scratch.reserve((size_t)streaming_slots * 4 * vec_stride * esz));
+  }
   MS_CUDA(g, g->tasks.reserve(tasks.size() * sizeof(Task)));
   MS_CUDA(g, g->partial.reserve((size_t)ntasks * sizeof(double)));
   MS_CUDA(g, g->ctl.reserve(L.bytes));
@@ -516,7 +547,60 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
     int sweeps_timed = 0;
     auto t_start = std::chrono::steady_clock::now();
     long long launched = 0;  // sweeps launched
+    if (!cands.empty()) {
+      // autotuning: sweep 0 with the model's favourite (x^0 leaves some blocks
+      // trivial), then one real sweep per candidate timed with CUDA events
+      std::vector<cudaEvent_t> tev(2 * cands.size());
+      struct TevGuard {
+        std::vector<cudaEvent_t>* v;
+        ~TevGuard() {
+          for (cudaEvent_t e : *v)
+            if (e) cudaEventDestroy(e);
+        }
+      } tevg{&tev};
+      for (auto& e : tev) MS_CUDA(g, cudaEventCreate(&e));
+      auto sweep_with = [&](const LaunchShape& sh) -> cudaError_t {
+        return sh.variant >= 0 ? launch_res_sweep(sh.variant, sh.cluster, sh.slots, sh.smem, sa, stream)
+                               : launch_sweep(prec, sh.threads, sh.cluster, sh.slots, sa, stream);
+      };
+      MS_CUDA(g, sweep_with(cands[0]));
+      MS_CUDA(g, launch_check(ca, stream));
+      for (size_t i = 0; i < cands.size(); ++i) {
+        MS_CUDA(g, cudaEventRecord(tev[2 * i], stream));
+        MS_CUDA(g, sweep_with(cands[i]));
+        MS_CUDA(g, cudaEventRecord(tev[2 * i + 1], stream));
+        MS_CUDA(g, launch_check(ca, stream));
+      }
+      launched += 1 + (long long)cands.size();
+      launches += 2 * (1 + (int)cands.size());
+      MS_CUDA(g, cudaMemcpyAsync(h_state.data(), rhs_state, g->nrhs * sizeof(int), cudaMemcpyDeviceToHost, stream));
+      MS_CUDA(g, cudaMemcpyAsync(h_flags, &ctl->all_done, sizeof(int), cudaMemcpyDeviceToHost, stream));
+      MS_CUDA(g, cudaMemcpyAsync(h_flags + 1, &ctl->err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+      MS_CUDA(g, cudaStreamSynchronize(stream));
+      if (h_flags[1]) return fail(g, MS_ERR_CUDA, "ms_solve: device error word 0x%x", h_flags[1]);
+      float best_t = 1e30f;
+      const bool verbose = std::getenv("MS_TUNE_VERBOSE") != nullptr;
+      for (size_t i = 0; i < cands.size(); ++i) {
+        float t = 0.f;
+        MS_CUDA(g, cudaEventElapsedTime(&t, tev[2 * i], tev[2 * i + 1]));
+        if (verbose)
+          std::fprintf(stderr, "ms tune: variant %d cluster %d threads %d slots %d smem %zu est %.3g -> %.3f ms\n",
+                       cands[i].variant, cands[i].cluster, cands[i].threads, cands[i].slots, cands[i].smem,
+                       cands[i].est, t);
+        if (t < best_t) {
+          best_t = t;
+          shape = cands[i];
+        }
+      }
+      // keep the measurement only if every rhs was still being solved throughout
+      bool clean = true;
+      for (int r = 0; r < g->nrhs; ++r)
+        if (h_state[r] != kActive) clean = false;
+      if (clean) g->tuner.best[sig] = shape;
+      if (h_flags[0]) chunk = 0;  // finished during tuning
+    }
     for (;;) {
+      if (chunk == 0) break;
       const long long remaining = (long long)o.outer_maxit + 1 - launched;
       if (remaining <= 0) break;
       const int n = (int)std::min<long long>(chunk, remaining);

@@ -78,7 +78,7 @@ __device__ __forceinline__ void zero_smem(float4* p, int n4) {
   for (int i = threadIdx.x; i < n4; i += NT) p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-template <int NT, int KC, int ZS>
+template <int NT, int KC, int ZS, bool DS>
 __global__ void __launch_bounds__(NT, 1) res_sweep_kernel(const SweepArgs a, int smem_f4) {
   extern __shared__ float4 dyn4[];
   float* sp = reinterpret_cast<float*>(dyn4);
@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(NT, 1) res_sweep_kernel(const SweepArgs a, int
       const int spr = (tk.bx + 3) >> 2;
       const int nzs_max = (tk.bz + (int)csize - 1) / (int)csize;
       if (tk.bz < (int)csize || nzs_max > ZS || spr * tk.by > KC * NT ||
-          res_smem_floats(tk.bx, tk.by, ZS) > 4LL * smem_f4) {
+          res_smem_floats(tk.bx, tk.by, ZS, DS) > 4LL * smem_f4) {
         if (tid == 0) atomicOr(a.err, kErrGeometry);
         continue;
       }
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(NT, 1) res_sweep_kernel(const SweepArgs a, int
     const double* __restrict__ xr = xin + rb;
     const double* __restrict__ fr = a.f ? a.f + rb : nullptr;
     const double* __restrict__ br = a.bnd ? a.bnd + (long long)tk.rhs * G.nbnd : nullptr;
-    float4 r4[KC][ZS], d4[KC][ZS];
+    float4 r4[KC][ZS], d4[DS ? 1 : KC][DS ? 1 : ZS];
     double red0[2];
     {
       double s64;
@@ -142,11 +142,12 @@ __global__ void __launch_bounds__(NT, 1) res_sweep_kernel(const SweepArgs a, int
     if (rank == 0 && tid == 0) a.partial[t] = red0[0];
     int m = 0;
     if (!residual_only)
-      m = resident_cg<NT, KC, ZS>(r4, d4, g, s, sp, (float)red0[1], (float)a.inner_rtol, a.inner_maxit, rred, rank,
-                                  csize);
-    // every cluster barrier of this task is behind us: the smem can be cleared for the next one
-    zero_smem<NT>(dyn4, smem_f4);
-    if (residual_only) continue;
+      m = resident_cg<NT, KC, ZS, DS>(r4, d4, g, s, sp, (float)red0[1], (float)a.inner_rtol, a.inner_maxit, rred,
+                                      rank, csize);
+    if (residual_only) {
+      zero_smem<NT>(dyn4, smem_f4);
+      continue;
+    }
     double* __restrict__ xo = xout + rb;
 #pragma unroll
     for (int kk = 0; kk < KC; ++kk) {
@@ -157,7 +158,9 @@ __global__ void __launch_bounds__(NT, 1) res_sweep_kernel(const SweepArgs a, int
       for (int z = 0; z < ZS; ++z) {
         if (z >= g.nzs) continue;
         const long long gi0 = (long long)(tk.oz + g.z0 + z) * nxy + row;
-        const float4 d = d4[kk][z];
+        float4 d;
+        if constexpr (DS) d = *d_slot<NT, KC, ZS, DS>(sp, g, z, s.st[kk]);
+        else d = d4[kk][z];
         const float dv[4] = {d.x, d.y, d.z, d.w};
 #pragma unroll
         for (int l = 0; l < 4; ++l) {
@@ -166,6 +169,10 @@ __global__ void __launch_bounds__(NT, 1) res_sweep_kernel(const SweepArgs a, int
         }
       }
     }
+    // every cluster barrier of this task is behind us and d has been consumed:
+    // the smem can be cleared for the next task
+    __syncthreads();
+    zero_smem<NT>(dyn4, smem_f4);
     if (rank == 0 && tid == 0 && m > 0) {
       atomicAdd(a.inner_count + 2 * tk.rhs, (unsigned long long)m);
       atomicAdd(a.inner_count + 2 * tk.rhs + 1, (unsigned long long)m * (unsigned long long)tk.bx * tk.by * tk.bz);
@@ -176,14 +183,16 @@ __global__ void __launch_bounds__(NT, 1) res_sweep_kernel(const SweepArgs a, int
 // ---------------------------------------------------------------- variants
 // (NT threads, KC strips per thread, ZS planes per CTA at most)
 struct ResVariant {
-  int nt, kc, zs;
+  int nt, kc, zs, ds;
 };
-static const ResVariant kResVariants[] = {{512, 2, 4}, {512, 1, 8}, {256, 2, 4}, {256, 1, 8}, {512, 4, 2}};
+static const ResVariant kResVariants[] = {{512, 2, 4, 0},  {512, 1, 8, 0},  {256, 2, 4, 0}, {256, 1, 8, 0},
+                                          {512, 4, 2, 0},  {1024, 1, 4, 1}, {1024, 2, 2, 1}, {1024, 1, 8, 1},
+                                          {512, 2, 4, 1}};
 constexpr int kNumResVariants = sizeof(kResVariants) / sizeof(kResVariants[0]);
 
-template <int NT, int KC, int ZS>
+template <int NT, int KC, int ZS, bool DS>
 static cudaError_t prep_res(int cluster, size_t smem_bytes, void** fn) {
-  auto kern = res_sweep_kernel<NT, KC, ZS>;
+  auto kern = res_sweep_kernel<NT, KC, ZS, DS>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
   if (e != cudaSuccess) return e;
   if (cluster > 8) {
@@ -196,21 +205,26 @@ static cudaError_t prep_res(int cluster, size_t smem_bytes, void** fn) {
 
 static cudaError_t res_fn(int variant, int cluster, size_t smem_bytes, void** fn) {
   switch (variant) {
-    case 0: return prep_res<512, 2, 4>(cluster, smem_bytes, fn);
-    case 1: return prep_res<512, 1, 8>(cluster, smem_bytes, fn);
-    case 2: return prep_res<256, 2, 4>(cluster, smem_bytes, fn);
-    case 3: return prep_res<256, 1, 8>(cluster, smem_bytes, fn);
-    case 4: return prep_res<512, 4, 2>(cluster, smem_bytes, fn);
+    case 0: return prep_res<512, 2, 4, false>(cluster, smem_bytes, fn);
+    case 1: return prep_res<512, 1, 8, false>(cluster, smem_bytes, fn);
+    case 2: return prep_res<256, 2, 4, false>(cluster, smem_bytes, fn);
+    case 3: return prep_res<256, 1, 8, false>(cluster, smem_bytes, fn);
+    case 4: return prep_res<512, 4, 2, false>(cluster, smem_bytes, fn);
+    case 5: return prep_res<1024, 1, 4, true>(cluster, smem_bytes, fn);
+    case 6: return prep_res<1024, 2, 2, true>(cluster, smem_bytes, fn);
+    case 7: return prep_res<1024, 1, 8, true>(cluster, smem_bytes, fn);
+    case 8: return prep_res<512, 2, 4, true>(cluster, smem_bytes, fn);
     default: return cudaErrorInvalidValue;
   }
 }
 
 int res_variant_count() { return kNumResVariants; }
 
-void res_variant_info(int v, int* nt, int* kc, int* zs) {
+void res_variant_info(int v, int* nt, int* kc, int* zs, int* ds) {
   *nt = kResVariants[v].nt;
   *kc = kResVariants[v].kc;
   *zs = kResVariants[v].zs;
+  *ds = kResVariants[v].ds;
 }
 
 static void res_cfg(cudaLaunchConfig_t* cfg, cudaLaunchAttribute* at, int nt, int cluster, int slots, size_t smem,

@@ -31,7 +31,7 @@ struct ResGeo {
   int bx, by, bz;
   int spr;      // strips per row = ceil(bx / 4)
   int nstrips;  // spr * by
-  int rp;       // smem row pitch in floats: 4 + 4*spr + 4
+  int rp;       // smem row pitch in floats: 4 zero floats + 4*spr (the next row's zeros pad the right end)
   int ps;       // smem plane stride in floats: (by + 2) * rp
   int z0, nzs;  // own planes
 };
@@ -43,18 +43,20 @@ __device__ __forceinline__ ResGeo make_res_geo(int bx, int by, int bz, unsigned 
   g.bz = bz;
   g.spr = (bx + 3) >> 2;
   g.nstrips = g.spr * by;
-  g.rp = 4 * g.spr + 8;
-  g.ps = (by + 2) * g.rp;
+  g.rp = 4 * g.spr + 4;
+  g.ps = (by + 2) * g.rp + 4;
   g.z0 = (int)(((long long)bz * rank) / csize);
   g.nzs = (int)(((long long)bz * (rank + 1)) / csize) - g.z0;
   return g;
 }
 
-// floats of dynamic shared memory for a geometry: p (nzs_max + 2 planes) and 2 r-halo planes
-__host__ __device__ inline long long res_smem_floats(int bx, int by, int nzs_max) {
-  const long long rp = 4 * ((bx + 3) / 4) + 8;
-  const long long ps = (by + 2) * rp;
-  return (nzs_max + 4) * ps;
+// floats of dynamic shared memory: p (zs + 2 planes), 2 r-halo planes, and
+// (d_in_smem) d as zs compact planes of 4*spr*by floats.
+__host__ __device__ inline long long res_smem_floats(int bx, int by, int zs, bool d_in_smem) {
+  const long long spr = (bx + 3) / 4;
+  const long long rp = 4 * spr + 4;
+  const long long ps = (by + 2) * rp + 4;  // + the right pad of the last row
+  return (zs + 4) * ps + (d_in_smem ? zs * 4 * spr * by : 0);
 }
 
 __device__ __forceinline__ void st_cluster_v4(float* local, unsigned rank, float4 v) {
@@ -165,8 +167,17 @@ struct ResRed {
 // cluster barrier of the residual reduction), p planes are zero.  Returns
 // m; d4 holds the correction when m > 0.  Scalars are FP32 and computed
 // identically by every thread of the cluster.
-template <int NT, int KC, int ZS>
-__device__ int resident_cg(float4 (&r4)[KC][ZS], float4 (&d4)[KC][ZS], const ResGeo& g, const Strips<KC>& s,
+// DS: d lives in shared memory (compact planes after the r-halo planes,
+// float4 per strip, index z * nstrips + strip) instead of registers, which
+// halves the registers a thread needs and lets a CTA run 1024 threads.
+template <int NT, int KC, int ZS, bool DS>
+__device__ __forceinline__ float4* d_slot(float* sp, const ResGeo& g, int z, int st) {
+  return reinterpret_cast<float4*>(sp + (long long)(ZS + 4) * g.ps) + (long long)z * g.nstrips + st;
+}
+
+template <int NT, int KC, int ZS, bool DS>
+__device__ int resident_cg(float4 (&r4)[KC][ZS], float4 (&d4)[DS ? 1 : KC][DS ? 1 : ZS], const ResGeo& g,
+                           const Strips<KC>& s,
                            float* sp, float gamma0, float inner_rtol, int inner_maxit, ResRed& rr, unsigned rank,
                            unsigned csize) {
   float* rh_lo = sp + (long long)(ZS + 2) * g.ps;  // neighbour below's top plane of r
@@ -195,9 +206,12 @@ __device__ int resident_cg(float4 (&r4)[KC][ZS], float4 (&d4)[KC][ZS], const Res
                              fmaf(beta, po.w, r.w)));
       }
     }
-    for (int st = tid; st < g.nstrips; st += NT) {
-      const int y = st / g.spr, xs = st - y * g.spr;
-      const int o = (y + 1) * g.rp + 4 + 4 * xs;
+    // halo planes have the layout of the own planes: each thread updates its own strips there
+    // (not unrolled: keeps the register count of the 512-thread variants under their cap)
+#pragma unroll 1
+    for (int k = 0; k < KC; ++k) {
+      if (!s.msk[k]) continue;
+      const int o = s.off[k];
       if (has_lo) {
         const float4 po = lds4(p_lo + o), r = lds4(rh_lo + o);
         sts4(p_lo + o, make_float4(fmaf(beta, po.x, r.x), fmaf(beta, po.y, r.y), fmaf(beta, po.z, r.z),
@@ -246,10 +260,19 @@ __device__ int resident_cg(float4 (&r4)[KC][ZS], float4 (&d4)[KC][ZS], const Res
         const float* cp = base + (long long)(z + 1) * g.ps;
         const float4 zp = lds4(cp + g.ps);
         const float4 q = mask4(stencil4(cp, g.rp, c, zm, zp, lft, rgt), s.msk[k]);
-        float4 d = d4[k][z];
-        if (m == 0) d = make_float4(0.f, 0.f, 0.f, 0.f);
-        d4[k][z] = make_float4(fmaf(alpha, c.x, d.x), fmaf(alpha, c.y, d.y), fmaf(alpha, c.z, d.z),
-                               fmaf(alpha, c.w, d.w));
+        if constexpr (DS) {
+          if (s.msk[k]) {
+            float4* dp = d_slot<NT, KC, ZS, DS>(sp, g, z, s.st[k]);
+            const float4 d = (m == 0) ? make_float4(0.f, 0.f, 0.f, 0.f) : *dp;
+            *dp = make_float4(fmaf(alpha, c.x, d.x), fmaf(alpha, c.y, d.y), fmaf(alpha, c.z, d.z),
+                              fmaf(alpha, c.w, d.w));
+          }
+        } else {
+          float4 d = d4[k][z];
+          if (m == 0) d = make_float4(0.f, 0.f, 0.f, 0.f);
+          d4[k][z] = make_float4(fmaf(alpha, c.x, d.x), fmaf(alpha, c.y, d.y), fmaf(alpha, c.z, d.z),
+                                 fmaf(alpha, c.w, d.w));
+        }
         float4 r = r4[k][z];
         r = make_float4(fmaf(-alpha, q.x, r.x), fmaf(-alpha, q.y, r.y), fmaf(-alpha, q.z, r.z),
                         fmaf(-alpha, q.w, r.w));

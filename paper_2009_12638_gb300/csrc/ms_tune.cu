@@ -19,10 +19,14 @@ static int max_clusters(Tuner& t, int prec, int mode, int threads, int cluster, 
   return 0;
 }
 
-static long long res_smem_bytes(const std::vector<Task>& tasks, int zs) {
-  long long ps = 0;
-  for (const Task& k : tasks) ps = std::max(ps, (long long)(k.by + 2) * (4 * ((k.bx + 3) / 4) + 8));
-  return (zs + 4) * ps * 4;
+static long long res_smem_bytes(const std::vector<Task>& tasks, int zs, int ds) {
+  long long mx = 0;
+  for (const Task& k : tasks) {
+    const long long spr = (k.bx + 3) / 4;
+    const long long ps = (k.by + 2) * (4 * spr + 4) + 4;
+    mx = std::max(mx, (zs + 4) * ps + (ds ? zs * 4 * spr * k.by : 0));
+  }
+  return mx * 4;
 }
 
 // Resident engine: every block must fit the variant at cluster size c.
@@ -35,17 +39,15 @@ static bool res_fits(const std::vector<Task>& tasks, int nt, int kc, int zs, int
   return true;
 }
 
-static int choose_resident(Tuner& t, const std::vector<Task>& tasks, long long maxpts, int req_cluster,
-                           int req_threads, int req_slots, LaunchShape* out) {
+static void list_resident(Tuner& t, const std::vector<Task>& tasks, long long maxpts, int req_cluster,
+                          int req_threads, int req_slots, std::vector<LaunchShape>* out) {
   const int ntasks = (int)tasks.size();
-  double best = 1e300;
-  bool found = false;
   for (int v = 0; v < res_variant_count(); ++v) {
-    int nt, kc, zs;
-    res_variant_info(v, &nt, &kc, &zs);
+    int nt, kc, zs, ds;
+    res_variant_info(v, &nt, &kc, &zs, &ds);
     if (req_threads && req_threads != nt) continue;
-    const long long smem = res_smem_bytes(tasks, zs);
-    if (smem > 200 * 1024) continue;
+    const long long smem = res_smem_bytes(tasks, zs, ds);
+    if (smem > 220 * 1024) continue;
     for (int c = 1; c <= kMaxCluster; ++c) {
       if (req_cluster && c != req_cluster) continue;
       if (!res_fits(tasks, nt, kc, zs, c)) continue;
@@ -62,50 +64,29 @@ static int choose_resident(Tuner& t, const std::vector<Task>& tasks, long long m
         t.occ[key] = occ;
       }
       if (occ < 1) continue;
-      const int slots = req_slots ? std::min(req_slots, occ) : std::min(occ, ntasks);
+      LaunchShape r;
+      r.variant = v;
+      r.cluster = c;
+      r.threads = nt;
+      r.slots = req_slots ? std::min(req_slots, occ) : std::min(occ, ntasks);
+      r.smem = (size_t)smem;
       // rounds of the task queue x points each CTA handles per round
-      const double rounds = std::ceil((double)ntasks / slots);
-      const double est = rounds * ((double)maxpts / c) * (1.0 + 0.02 * c);
-      if (est < best) {
-        best = est;
-        found = true;
-        out->variant = v;
-        out->cluster = c;
-        out->threads = nt;
-        out->slots = slots;
-        out->smem = (size_t)smem;
-      }
+      const double rounds = std::ceil((double)ntasks / r.slots);
+      r.est = rounds * ((double)maxpts / c) * (1.0 + 0.02 * c);
+      out->push_back(r);
     }
   }
-  return found ? 0 : -1;
 }
 
-int choose_shape(Tuner& t, int prec, int mode, int engine, const std::vector<Task>& tasks, long long maxpts,
-                 int req_cluster, int req_threads, int req_slots, LaunchShape* out) {
+static int streaming_shape(Tuner& t, int prec, int mode, const std::vector<Task>& tasks, long long maxpts,
+                           int req_cluster, int req_threads, int req_slots, int threads, LaunchShape* out) {
   const int ntasks = (int)tasks.size();
-  if (prec == 1 && mode == 0 && engine != 1) {
-    LaunchShape r;
-    if (choose_resident(t, tasks, maxpts, req_cluster, req_threads, req_slots, &r) == 0) {
-      *out = r;
-      return 0;
-    }
-    if (engine == 2) return (int)cudaErrorInvalidConfiguration;  // resident requested but nothing fits
-  }
-  double mean_bz = 0.0, mean_plane = 0.0;
-  for (const Task& k : tasks) {
-    mean_bz += k.bz;
-    mean_plane += (double)k.bx * k.by;
-  }
+  double mean_bz = 0.0;
+  for (const Task& k : tasks) mean_bz += k.bz;
   mean_bz /= std::max(1, ntasks);
-  mean_plane /= std::max(1, ntasks);
   LaunchShape s;
-  s.threads = req_threads ? req_threads : (mean_plane >= 2048 ? 512 : 256);
-  if (req_cluster) {
-    s.cluster = req_cluster;
-  } else {
-    int c = (int)(mean_bz / 6.0);
-    s.cluster = std::max(1, std::min(8, c));
-  }
+  s.threads = req_threads ? req_threads : threads;
+  s.cluster = req_cluster ? req_cluster : std::max(1, std::min(8, (int)(mean_bz / 6.0)));
   int maxc = 0;
   int e = max_clusters(t, prec, mode, s.threads, s.cluster, &maxc);
   if (e) return e;
@@ -117,13 +98,53 @@ int choose_shape(Tuner& t, int prec, int mode, int engine, const std::vector<Tas
     if (prec == 1) {
       // keep the CG vectors of the blocks in flight inside L2 (~80 MB usable)
       const double per = 4.0 * (double)maxpts * 4.0;
-      int l2cap = (int)std::max(1.0, 80.0e6 / per);
-      int fill = (152 + s.cluster - 1) / s.cluster;
+      const int l2cap = (int)std::max(1.0, 80.0e6 / per);
+      const int fill = (152 + s.cluster - 1) / s.cluster;
       g = std::min(g, std::max(l2cap, fill));
     }
     s.slots = std::max(1, g);
   }
+  s.variant = -1;
+  s.est = 4.0 * std::ceil((double)ntasks / s.slots) * ((double)maxpts / s.cluster);  // ~4x slower than on chip
   *out = s;
+  return 0;
+}
+
+std::vector<long long> signature(int prec, int mode, int engine, const std::vector<Task>& tasks) {
+  std::vector<long long> sig = {prec, mode, engine, (long long)tasks.size()};
+  std::vector<long long> shapes;
+  for (const Task& k : tasks) shapes.push_back(((long long)k.bx << 40) | ((long long)k.by << 20) | k.bz);
+  std::sort(shapes.begin(), shapes.end());
+  sig.insert(sig.end(), shapes.begin(), shapes.end());
+  return sig;
+}
+
+int list_shapes(Tuner& t, int prec, int mode, int engine, const std::vector<Task>& tasks, long long maxpts,
+                int req_cluster, int req_threads, int req_slots, std::vector<LaunchShape>* out) {
+  out->clear();
+  if (prec == 1 && mode == 0 && engine != 1) {
+    list_resident(t, tasks, maxpts, req_cluster, req_threads, req_slots, out);
+    std::stable_sort(out->begin(), out->end(),
+                     [](const LaunchShape& a, const LaunchShape& b) { return a.est < b.est; });
+    if (engine == 2) return out->empty() ? (int)cudaErrorInvalidConfiguration : 0;
+  }
+  int last = 0;
+  for (int threads : {512, 1024}) {
+    if (req_threads && req_threads != threads && threads != 512) continue;
+    LaunchShape s;
+    last = streaming_shape(t, prec, mode, tasks, maxpts, req_cluster, req_threads, req_slots, threads, &s);
+    if (last == 0) out->push_back(s);
+    if (req_threads) break;
+  }
+  return out->empty() ? (last ? last : (int)cudaErrorInvalidConfiguration) : 0;
+}
+
+int choose_shape(Tuner& t, int prec, int mode, int engine, const std::vector<Task>& tasks, long long maxpts,
+                 int req_cluster, int req_threads, int req_slots, LaunchShape* out) {
+  std::vector<LaunchShape> all;
+  const int rc = list_shapes(t, prec, mode, engine, tasks, maxpts, req_cluster, req_threads, req_slots, &all);
+  if (rc) return rc;
+  *out = all.front();
   return 0;
 }
 

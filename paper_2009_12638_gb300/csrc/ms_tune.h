@@ -17,12 +17,13 @@ struct LaunchShape {
   int slots = 1;
   int variant = -1;   // >= 0: resident engine variant (ms_resident.cu); -1: streaming engine
   size_t smem = 0;    // dynamic shared memory bytes (resident engine)
+  double est = 0.0;   // model estimate used to rank shapes before measuring
 };
 
 struct Tuner {
-  // cache of maxActiveClusters per (prec, mode, threads, cluster)
+  // cache of maxActiveClusters per (kernel kind, smem, threads, cluster)
   std::map<std::tuple<int, int, int, int>, int> occ;
-  // measured best shape per problem signature
+  // measured best shape per problem signature (see signature())
   std::map<std::vector<long long>, LaunchShape> best;
   void release() {
     occ.clear();
@@ -30,8 +31,17 @@ struct Tuner {
   }
 };
 
-// Picks a shape; explicit non-zero requests are honoured.  Returns a
-// cudaError_t value (0 on success).
+// Problem signature for the cache of measured shapes: precision, mode,
+// engine request, and the sorted multiset of block shapes.
+std::vector<long long> signature(int prec, int mode, int engine, const std::vector<Task>& tasks);
+
+// Every launchable shape for the problem, best model estimate first (the
+// resident engine's shapes, when it applies, precede the streaming ones).
+// Explicit non-zero requests restrict the list.  Returns a cudaError_t value.
+int list_shapes(Tuner& t, int prec, int mode, int engine, const std::vector<Task>& tasks, long long maxpts,
+                int req_cluster, int req_threads, int req_slots, std::vector<LaunchShape>* out);
+
+// The first shape of list_shapes.
 int choose_shape(Tuner& t, int prec, int mode, int engine, const std::vector<Task>& tasks, long long maxpts,
                  int req_cluster, int req_threads, int req_slots, LaunchShape* out);
 
