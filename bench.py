@@ -38,6 +38,29 @@ WORKLOAD = "laplace256_u11"
 # writes x (20 B): 32 B per point at FP32 (the FP64 r/d add 8 B).
 INNER_BYTES = {"mixed": 24.0, "fp64": 48.0}
 OUTER_BYTES = {"mixed": 32.0, "fp64": 40.0}
+# DRAM traffic per launch of the dominant kernel, from one ncu capture, with
+# the hash of the kernel sources it was taken on (null once they change)
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "res_sweep_laplace256_traffic.json")
+KERNEL_SOURCES = ["ms_resident.cu", "ms_resident.cuh", "ms_device.cuh", "ms_cg.cuh", "ms_internal.h"]
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2009_12638_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel_name):
+    try:
+        rec = json.load(open(TRAFFIC_FILE))
+    except Exception:
+        return None, None
+    if rec.get("source_hash") != kernel_source_hash() or rec.get("kernel") != kernel_name:
+        return None, rec.get("source_hash")
+    return float(rec["dram_bytes_per_launch"]), rec.get("source_hash")
 
 
 def parse():
@@ -51,6 +74,8 @@ def parse():
     ap.add_argument("--mode", default="sync", choices=["sync", "async"])
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64-sync and async comparison solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--sweeps", type=int, default=0,
+                    help="profiling aid: run exactly this many outer sweeps once (no warm-up, no timing) and exit")
     return ap.parse_args()
 
 
@@ -187,6 +212,14 @@ def main():
         x.zero_()
         return grid.solve(bnd=bnd, out=x, **dict(opts, **extra))
 
+    if args.sweeps:
+        # a short, fixed run for ncu captures: the shape the autotuner would pick, plain launches
+        _, st = solve_once(outer_tol=0.0, outer_maxit=args.sweeps, use_graph=False)
+        torch.cuda.synchronize(dev)
+        print(json.dumps({"sweeps": args.sweeps, "status": st.status_name, "engine": st.engine,
+                          "shape": [st.cluster, st.threads, st.slots], "time_ms": st.time_ms}))
+        return
+
     for _ in range(max(args.warmup, 3)):
         _, st = solve_once()
         assert st.status == 0, st
@@ -254,11 +287,15 @@ def main():
     except Exception:
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
+    kname = "res_sweep_kernel" if sp.engine == 2 else "sweep_kernel"
+    traffic, _ = measured_traffic(kname)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": f"sweep_kernel<{'float' if args.precision == 'mixed' else 'double'}>",
-                "per_launch_ms": per_launch_ms, "launches_timed": sp.sweep_launches,
-                "alg_bytes_per_launch": alg_bytes / sweeps,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s"}
+                "traffic": traffic, "kernel": kname, "per_launch_ms": per_launch_ms,
+                "launches_timed": sp.sweep_launches, "alg_bytes_per_launch": alg_bytes / sweeps,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s",
+                "note": "achieved = algorithmic bytes (24 B per inner LUP, 32 B per point per sweep) / launch "
+                        "time; the resident kernel keeps the CG state on chip, so its DRAM traffic (ncu) is "
+                        "~1% of these bytes and the bound is shared memory and latency, not HBM"}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -268,6 +305,7 @@ def main():
                                   "U(-1,1) seed 2009, x0=0, inner CG <=50 its rtol 1e-6, outer rel tol 1e-8",
                       "precision": args.precision, "mode": args.mode,
                       "launch_shape": {"cluster": st0.cluster, "threads": st0.threads, "slots": st0.slots},
+                      "kernel_source_hash": kernel_source_hash(),
                       "l2": "flushed (256 MB write) between timed solves"},
            "time_to_tol_s": total_ms / args.steps / 1e3, "outer_its": st0.outer_its, "inner_its": st0.inner_its,
            "rel_residual": max(s.rel_residual for s in stats), "gpu_launches": launches,

@@ -106,6 +106,7 @@ typedef struct {
   double* per_rhs_rel;         /* HOST, optional [nrhs]: filled if non-NULL */
   double sweep_ms;             /* with opts.profile: summed device time of the sweep kernels */
   int sweep_launches;          /* with opts.profile: sweep kernels timed */
+  int engine;                  /* inner-CG engine used: 1 streaming, 2 resident */
 } ms_stats;
 
 /* Number of doubles in one rhs's packed boundary array. */

@@ -49,6 +49,7 @@ class SolveStats:
     per_rhs_rel: list
     sweep_ms: float = 0.0
     sweep_launches: int = 0
+    engine: int = 0
     history: np.ndarray | None = None
 
     @property
@@ -201,7 +202,7 @@ class Grid:
             self._check(rc)
         stats = SolveStats(rc, st.outer_its, st.inner_its, st.lups, st.rel_residual, st.time_ms, st.launches,
                            st.cluster, st.threads, st.slots, list(per_its), list(per_rel), st.sweep_ms,
-                           st.sweep_launches)
+                           st.sweep_launches, st.engine)
         if hist is not None:
             stats.history = hist
         return out, stats

@@ -68,6 +68,7 @@ class Stats(ctypes.Structure):
         ("per_rhs_rel", ctypes.POINTER(ctypes.c_double)),
         ("sweep_ms", ctypes.c_double),
         ("sweep_launches", ctypes.c_int),
+        ("engine", ctypes.c_int),
     ]
 
 

@@ -737,6 +737,7 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
     st->cluster = shape.cluster;
     st->threads = shape.threads;
     st->slots = shape.slots;
+    st->engine = shape.variant >= 0 ? 2 : 1;
   }
   return status;
 }

@@ -144,10 +144,10 @@ __global__ void __launch_bounds__(NT, 1) res_sweep_kernel(const SweepArgs a, int
     if (!residual_only)
       m = resident_cg<NT, KC, ZS, DS>(r4, d4, g, s, sp, (float)red0[1], (float)a.inner_rtol, a.inner_maxit, rred,
                                       rank, csize);
-    if (residual_only) {
-      zero_smem<NT>(dyn4, smem_f4);
-      continue;
-    }
+    // every cluster barrier of this task is behind us: with d in registers the
+    // smem can be cleared for the next task right away (with d in smem, after the update)
+    if (residual_only || !DS) zero_smem<NT>(dyn4, smem_f4);
+    if (residual_only) continue;
     double* __restrict__ xo = xout + rb;
 #pragma unroll
     for (int kk = 0; kk < KC; ++kk) {
@@ -169,10 +169,10 @@ __global__ void __launch_bounds__(NT, 1) res_sweep_kernel(const SweepArgs a, int
         }
       }
     }
-    // every cluster barrier of this task is behind us and d has been consumed:
-    // the smem can be cleared for the next task
-    __syncthreads();
-    zero_smem<NT>(dyn4, smem_f4);
+    if constexpr (DS) {
+      __syncthreads();  // d has been consumed by every thread
+      zero_smem<NT>(dyn4, smem_f4);
+    }
     if (rank == 0 && tid == 0 && m > 0) {
       atomicAdd(a.inner_count + 2 * tk.rhs, (unsigned long long)m);
       atomicAdd(a.inner_count + 2 * tk.rhs + 1, (unsigned long long)m * (unsigned long long)tk.bx * tk.by * tk.bz);

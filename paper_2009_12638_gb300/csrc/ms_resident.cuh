@@ -34,6 +34,7 @@ struct ResGeo {
   int rp;       // smem row pitch in floats: 4 zero floats + 4*spr (the next row's zeros pad the right end)
   int ps;       // smem plane stride in floats: (by + 2) * rp
   int z0, nzs;  // own planes
+  unsigned spr_magic;  // ceil(2^32 / spr): st / spr == __umulhi(st, spr_magic) for st < 2^15
 };
 
 __device__ __forceinline__ ResGeo make_res_geo(int bx, int by, int bz, unsigned rank, unsigned csize) {
@@ -45,6 +46,7 @@ __device__ __forceinline__ ResGeo make_res_geo(int bx, int by, int bz, unsigned 
   g.nstrips = g.spr * by;
   g.rp = 4 * g.spr + 4;
   g.ps = (by + 2) * g.rp + 4;
+  g.spr_magic = (unsigned)((0x100000000ULL + (unsigned long long)g.spr - 1) / (unsigned long long)g.spr);
   g.z0 = (int)(((long long)bz * rank) / csize);
   g.nzs = (int)(((long long)bz * (rank + 1)) / csize) - g.z0;
   return g;
@@ -206,12 +208,10 @@ __device__ int resident_cg(float4 (&r4)[KC][ZS], float4 (&d4)[DS ? 1 : KC][DS ? 
                              fmaf(beta, po.w, r.w)));
       }
     }
-    // halo planes have the layout of the own planes: each thread updates its own strips there
-    // (not unrolled: keeps the register count of the 512-thread variants under their cap)
-#pragma unroll 1
-    for (int k = 0; k < KC; ++k) {
-      if (!s.msk[k]) continue;
-      const int o = s.off[k];
+    // halo planes: every strip of the plane, thread-strided (y = st / spr by multiply-high)
+    for (int st = tid; st < g.nstrips; st += NT) {
+      const int y = (int)__umulhi((unsigned)st, g.spr_magic), xs = st - y * g.spr;
+      const int o = (y + 1) * g.rp + 4 + 4 * xs;
       if (has_lo) {
         const float4 po = lds4(p_lo + o), r = lds4(rh_lo + o);
         sts4(p_lo + o, make_float4(fmaf(beta, po.x, r.x), fmaf(beta, po.y, r.y), fmaf(beta, po.z, r.z),

@@ -1,0 +1,118 @@
+"""Parity at the full workload sizes, in the launch configuration bench.py
+times, on outputs the oracle can produce within seconds: the first outer
+sweeps (every block's residual, inner CG and update), a sample of the
+right-hand sides, and properties that hold at any size (the true residual
+of a converged solve, the adjoint's finite-difference identity).
+
+Tolerances: FP64 sweeps follow the oracle's arithmetic up to rounding order
+(1e-11 relative); a mixed sweep is one FP32 CG solve per block, which agrees
+with the FP64 one to ~1e-5 relative after 50 iterations (2e-4 allowed).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2009_12638_gb300 import Grid, MsSolve, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _threads():
+    oracle.set_threads(oracle.max_threads())
+    yield
+    oracle.set_threads(1)
+
+
+def grid_for(cfg, nrhs=None):
+    g = Grid(cfg["nx"], cfg["ny"], cfg["nz"], cfg["nrhs"] if nrhs is None else nrhs)
+    return g.partition(len(cfg["cx"]) - 1, len(cfg["cy"]) - 1, len(cfg["cz"]) - 1, cfg["cx"], cfg["cy"], cfg["cz"])
+
+
+def rel_inf(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def oracle_sweeps(cfg, s, sweeps):
+    return oracle.solve(cfg["nx"], cfg["ny"], cfg["nz"], cfg["cx"], cfg["cy"], cfg["cz"], bnd=cfg["bnd"][s],
+                        outer_tol=0.0, outer_maxit=sweeps)
+
+
+def test_laplace256_first_sweeps_mixed_bench_shape():
+    cfg = inputs.make_config("laplace256_u11")
+    g = grid_for(cfg)
+    # the shape the autotuner picks for this workload on GB300 (resident engine, 16-CTA clusters)
+    x, st = g.solve(bnd=torch.from_numpy(cfg["bnd"]).cuda(), precision="mixed", cluster=16, threads=512,
+                    outer_tol=0.0, outer_maxit=2)
+    assert (st.cluster, st.threads) == (16, 512) and st.outer_its == 2
+    ref = oracle_sweeps(cfg, 0, 2)
+    assert rel_inf(x.cpu().numpy()[0], ref["x"]) <= 2e-4
+
+
+def test_laplace256_first_sweeps_fp64():
+    cfg = inputs.make_config("laplace256_u11")
+    g = grid_for(cfg)
+    x, st = g.solve(bnd=torch.from_numpy(cfg["bnd"]).cuda(), precision="fp64", outer_tol=0.0, outer_maxit=2)
+    ref = oracle_sweeps(cfg, 0, 2)
+    assert rel_inf(x.cpu().numpy()[0], ref["x"]) <= 1e-11
+    assert st.inner_its == ref["inner_its"]
+
+
+def test_laplace256_converged_true_residual():
+    cfg = inputs.make_config("laplace256_u11")
+    g = grid_for(cfg)
+    b = torch.from_numpy(cfg["bnd"]).cuda()
+    x, st = g.solve(bnd=b, precision="mixed")
+    assert st.status == 0 and st.rel_residual < 1e-8
+    assert g.residual(x, bnd=b)[0] < 1e-8
+
+
+def test_batched_uneven_first_sweep_sampled_rhs():
+    cfg = inputs.make_config("batched_uneven")
+    g = grid_for(cfg)
+    x, st = g.solve(bnd=torch.from_numpy(cfg["bnd"]).cuda(), precision="mixed", outer_tol=0.0, outer_maxit=1)
+    assert st.outer_its == 1
+    xs = x.cpu().numpy()
+    for s in (0, 15):
+        ref = oracle_sweeps(cfg, s, 1)
+        assert rel_inf(xs[s], ref["x"]) <= 2e-4, s
+
+
+def test_laplace512_first_sweep_sampled_rhs():
+    cfg = inputs.make_config("laplace512_async")
+    g = grid_for(cfg)
+    x, st = g.solve(bnd=torch.from_numpy(cfg["bnd"]).cuda(), precision="mixed", outer_tol=0.0, outer_maxit=1)
+    ref = oracle_sweeps(cfg, 3, 1)
+    assert rel_inf(x[3].cpu().numpy(), ref["x"]) <= 2e-4
+
+
+def test_adjoint128_central_fd():
+    cfg = inputs.make_config("adjoint128")
+    n = cfg["nx"]
+    g = grid_for(cfg)
+    f0 = torch.zeros((1, n, n, n), dtype=torch.float64, device="cuda")
+    g0 = torch.from_numpy(cfg["bnd"]).cuda()
+    target = torch.from_numpy(cfg["target"][None]).cuda()
+    opts = dict(precision="mixed", outer_tol=1e-12)
+    f = f0.clone().requires_grad_(True)
+    gb = g0.clone().requires_grad_(True)
+    u = MsSolve.apply(f, gb, g, opts)
+    (0.5 * ((u - target) ** 2).sum()).backward()
+    nprobe = 6
+    vf = inputs.gaussian_probes((1, n, n, n), nprobe, cfg["probe_seed"])
+    vg = inputs.gaussian_probes((1, g.nbnd), nprobe, cfg["probe_seed"] + 1)
+    theta = float(torch.linalg.vector_norm(g0))
+    for i in range(nprobe):
+        v_f = torch.from_numpy(vf[i]).cuda()
+        v_g = torch.from_numpy(vg[i]).cuda()
+        eps = 1e-2 * theta / float(torch.sqrt((v_f ** 2).sum() + (v_g ** 2).sum()))
+
+        def L(s):
+            uu, st = g.solve(f=f0 + s * v_f, bnd=g0 + s * v_g, **opts)
+            assert st.status == 0
+            return 0.5 * float(((uu - target) ** 2).sum())
+
+        fd = (L(eps) - L(-eps)) / (2 * eps)
+        ad = float((f.grad * v_f).sum() + (gb.grad * v_g).sum())
+        assert abs(ad - fd) <= 1e-6 * abs(fd), (i, ad, fd)
