@@ -834,7 +834,8 @@ int solve_async(ms_grid* g, const double* f, const double* bnd, double* x, const
   int status = MS_ERR_NOT_CONVERGED;
   auto t_start = std::chrono::steady_clock::now();
   for (int rel = 0; rel < 100000; ++rel) {
-    MS_CUDA(g, launch_async(prec, shape.threads, shape.cluster, shape.slots, a, stream));
+    MS_CUDA(g, shape.variant >= 0 ? launch_res_async(shape.variant, shape.cluster, shape.slots, shape.smem, a, stream)
+                                  : launch_async(prec, shape.threads, shape.cluster, shape.slots, a, stream));
     launches += 1;
     int rc = run_resid(g, f, bnd, x, norms, nullptr, stream);
     if (rc != MS_OK) return rc;

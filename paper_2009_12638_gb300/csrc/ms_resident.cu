@@ -6,6 +6,7 @@
 // writes r straight into registers, and the update reads d from registers.
 #include <cuda_runtime.h>
 
+#include "ms_async.cuh"
 #include "ms_device.cuh"
 #include "ms_internal.h"
 #include "ms_resident.cuh"
@@ -18,12 +19,14 @@ namespace ms {
 // magnitude; the boundary planes of r are pushed to the neighbour CTAs'
 // r-halo planes.  s64: FP64 sum of squares of the unscaled r; g32: FP32 sum
 // of squares of the scaled, rounded r.
-template <int NT, int KC, int ZS>
+// nb(x, y, z, gi, si, so): neighbour sums of block point (x, y, z) (block
+// coordinates, grid index gi) -- straight from x^k (sync) or through the
+// halo cache (async).
+template <int NT, int KC, int ZS, typename NB>
 __device__ __forceinline__ void resident_residual(float4 (&r4)[KC][ZS], const ResGeo& g, const Strips<KC>& s,
-                                                  const Task& tk, const Geo& G, const double* __restrict__ xr,
-                                                  const double* __restrict__ fr, const double* __restrict__ br,
-                                                  double scale, float* sp, unsigned rank, unsigned csize,
-                                                  double& s64, float& g32) {
+                                                  const Task& tk, const Geo& G, const double* xr,
+                                                  const double* __restrict__ fr, double scale, float* sp,
+                                                  unsigned rank, unsigned csize, double& s64, float& g32, NB&& nb) {
   float* rh_lo = sp + (long long)(ZS + 2) * g.ps;
   float* rh_hi = rh_lo + g.ps;
   const long long nxy = (long long)G.nx * G.ny;
@@ -46,7 +49,7 @@ __device__ __forceinline__ void resident_residual(float4 (&r4)[KC][ZS], const Re
             const int gx = gx0 + l;
             const long long gi = (long long)gz * nxy + (long long)gy * G.nx + gx;
             double si, so;
-            nbr_sums(G, xr, br, gx, gy, gz, gi, si, so);
+            nb(gx - tk.ox, gy - tk.oy, g.z0 + z, gi, si, so);
             const double bh = fr ? fr[gi] + so : so;
             const double rr = bh - (6.0 * xr[gi] - si);
             sl += rr * rr;
@@ -129,7 +132,10 @@ __global__ void __launch_bounds__(NT, 1) res_sweep_kernel(const SweepArgs a, int
     {
       double s64;
       float g32;
-      resident_residual<NT, KC, ZS>(r4, g, s, tk, G, xr, fr, br, scale, sp, rank, csize, s64, g32);
+      resident_residual<NT, KC, ZS>(r4, g, s, tk, G, xr, fr, scale, sp, rank, csize, s64, g32,
+                                    [&](int bxl, int byl, int bzl, long long gi, double& si, double& so) {
+                                      nbr_sums(G, xr, br, tk.ox + bxl, tk.oy + byl, tk.oz + bzl, gi, si, so);
+                                    });
       red0[0] = s64;
       red0[1] = (double)g32;
     }
@@ -180,6 +186,104 @@ __global__ void __launch_bounds__(NT, 1) res_sweep_kernel(const SweepArgs a, int
   }
 }
 
+// Asynchronous outer iteration with the on-chip inner CG (protocol in
+// ms_async.cuh): halo refresh, residual through the halo cache, resident CG,
+// in-place update fused with face publication, stale-estimate monitor.
+template <int NT, int KC, int ZS, bool DS>
+__global__ void __launch_bounds__(NT, 1) res_async_kernel(const AsyncArgs a, int smem_f4) {
+  extern __shared__ float4 dyn4[];
+  float* sp = reinterpret_cast<float*>(dyn4);
+  __shared__ RedSmem red;
+  __shared__ ResRed rred;
+  __shared__ int bc[2][32];
+  const unsigned rank = cl_rank(), csize = cl_size(), cid = cl_id(), ncl = cl_count();
+  const int tid = threadIdx.x;
+  const Geo G = a.g;
+  const long long nxy = (long long)G.nx * G.ny;
+  __shared__ unsigned snap[12];
+  AsyncCtl c = async_ctl_init(a, cid, ncl, snap);
+  zero_smem<NT>(dyn4, smem_f4);
+  for (;; c.par ^= 1) {
+    const int t = async_pick(a, c, bc, rank, csize, cid, ncl);
+    if (t < 0) break;
+    const Task tk = a.tasks[t];
+    {
+      const int spr = (tk.bx + 3) >> 2;
+      const int nzs_max = (tk.bz + (int)csize - 1) / (int)csize;
+      if (tk.bz < (int)csize || nzs_max > ZS || spr * tk.by > KC * NT ||
+          res_smem_floats(tk.bx, tk.by, ZS, DS) > 4LL * smem_f4 || face_size(0, tk.bx, tk.by, tk.bz) > a.face_stride ||
+          face_size(2, tk.bx, tk.by, tk.bz) > a.face_stride || face_size(4, tk.bx, tk.by, tk.bz) > a.face_stride) {
+        if (rank == 0 && tid == 0) {
+          atomicOr(a.err, kErrGeometry);
+          st_rlx_s32(a.stop, 1);
+        }
+        continue;
+      }
+    }
+    if (a.slow_block == tk.block && a.slow_ns > 0 && rank == 0 && tid == 0)
+      __nanosleep((unsigned)min(a.slow_ns, 1000000));
+    async_halo_refresh<NT>(a, tk, t, bc, c, rank, csize);
+    const int* hcur = bc[c.par] + 20;
+    const ResGeo g = make_res_geo(tk.bx, tk.by, tk.bz, rank, csize);
+    const Strips<KC> s = make_strips<NT, KC>(g);
+    const double scale = pow2_near(a.inv_bnorm[tk.rhs]), unscale = 1.0 / scale;
+    const long long rb = (long long)tk.rhs * G.npts;
+    double* xr = a.x + rb;
+    const double* __restrict__ fr = a.f ? a.f + rb : nullptr;
+    const double* __restrict__ br = a.bnd ? a.bnd + (long long)tk.rhs * G.nbnd : nullptr;
+    float4 r4[KC][ZS], d4[DS ? 1 : KC][DS ? 1 : ZS];
+    double red0[2];
+    {
+      double s64;
+      float g32;
+      resident_residual<NT, KC, ZS>(r4, g, s, tk, G, xr, fr, scale, sp, rank, csize, s64, g32,
+                                    [&](int bxl, int byl, int bzl, long long gi, double& si, double& so) {
+                                      async_nbr_sums(a, tk, t, hcur, xr, br, bxl, byl, bzl, gi, si, so);
+                                    });
+      red0[0] = s64;
+      red0[1] = (double)g32;
+    }
+    cluster_reduce<NT, 2>(red0, red.slots[0], red.wsum, rank, csize, [&](double (&tt)[2]) {
+      red.tot[0] = tt[0];
+      red.tot[1] = tt[1];
+    });
+    if (rank == 0 && tid == 0) st_rlx_f64(a.partial + t, red.tot[0]);
+    const int m = resident_cg<NT, KC, ZS, DS>(r4, d4, g, s, sp, (float)red.tot[1], (float)a.inner_rtol,
+                                              a.inner_maxit, rred, rank, csize);
+    if constexpr (!DS) zero_smem<NT>(dyn4, smem_f4);  // all cluster barriers of the CG are behind us
+    async_publish_begin(a, tk, t, bc, c, rank, csize);
+    const int* fslot = bc[c.par] + 26;
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk) {
+      if (!s.msk[kk]) continue;
+      const int y = s.st[kk] / g.spr, x0 = 4 * (s.st[kk] - y * g.spr);
+      const long long row = (long long)(tk.oy + y) * G.nx + tk.ox + x0;
+#pragma unroll
+      for (int z = 0; z < ZS; ++z) {
+        if (z >= g.nzs) continue;
+        const long long gi0 = (long long)(tk.oz + g.z0 + z) * nxy + row;
+        float4 d;
+        if constexpr (DS) d = *d_slot<NT, KC, ZS, DS>(sp, g, z, s.st[kk]);
+        else d = d4[kk][z];
+        const float dv[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          if (!(s.msk[kk] & (1u << l))) continue;
+          const double xn = (m > 0) ? xr[gi0 + l] + (double)dv[l] * unscale : xr[gi0 + l];
+          xr[gi0 + l] = xn;
+          async_face_store(a, tk, t, fslot, x0 + l, y, g.z0 + z, xn);
+        }
+      }
+    }
+    async_publish_end(a, tk, t, fslot, rank, m);
+    if constexpr (DS) {
+      __syncthreads();
+      zero_smem<NT>(dyn4, smem_f4);
+    }
+    async_monitor(a, rank);
+  }
+}
+
 // ---------------------------------------------------------------- variants
 // (NT threads, KC strips per thread, ZS planes per CTA at most)
 struct ResVariant {
@@ -191,8 +295,19 @@ static const ResVariant kResVariants[] = {{512, 2, 4, 0},  {512, 1, 8, 0},  {256
 constexpr int kNumResVariants = sizeof(kResVariants) / sizeof(kResVariants[0]);
 
 template <int NT, int KC, int ZS, bool DS>
-static cudaError_t prep_res(int cluster, size_t smem_bytes, void** fn) {
-  auto kern = res_sweep_kernel<NT, KC, ZS, DS>;
+static cudaError_t prep_res(int cluster, size_t smem_bytes, void** fn, bool async_mode) {
+  void (*kern)(const SweepArgs, int) = res_sweep_kernel<NT, KC, ZS, DS>;
+  void (*akern)(const AsyncArgs, int) = res_async_kernel<NT, KC, ZS, DS>;
+  if (async_mode) {
+    cudaError_t e = cudaFuncSetAttribute(akern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    if (e != cudaSuccess) return e;
+    if (cluster > 8) {
+      e = cudaFuncSetAttribute(akern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) return e;
+    }
+    *fn = (void*)akern;
+    return cudaSuccess;
+  }
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
   if (e != cudaSuccess) return e;
   if (cluster > 8) {
@@ -203,17 +318,17 @@ static cudaError_t prep_res(int cluster, size_t smem_bytes, void** fn) {
   return cudaSuccess;
 }
 
-static cudaError_t res_fn(int variant, int cluster, size_t smem_bytes, void** fn) {
+static cudaError_t res_fn(int variant, int cluster, size_t smem_bytes, void** fn, bool am = false) {
   switch (variant) {
-    case 0: return prep_res<512, 2, 4, false>(cluster, smem_bytes, fn);
-    case 1: return prep_res<512, 1, 8, false>(cluster, smem_bytes, fn);
-    case 2: return prep_res<256, 2, 4, false>(cluster, smem_bytes, fn);
-    case 3: return prep_res<256, 1, 8, false>(cluster, smem_bytes, fn);
-    case 4: return prep_res<512, 4, 2, false>(cluster, smem_bytes, fn);
-    case 5: return prep_res<1024, 1, 4, true>(cluster, smem_bytes, fn);
-    case 6: return prep_res<1024, 2, 2, true>(cluster, smem_bytes, fn);
-    case 7: return prep_res<1024, 1, 8, true>(cluster, smem_bytes, fn);
-    case 8: return prep_res<512, 2, 4, true>(cluster, smem_bytes, fn);
+    case 0: return prep_res<512, 2, 4, false>(cluster, smem_bytes, fn, am);
+    case 1: return prep_res<512, 1, 8, false>(cluster, smem_bytes, fn, am);
+    case 2: return prep_res<256, 2, 4, false>(cluster, smem_bytes, fn, am);
+    case 3: return prep_res<256, 1, 8, false>(cluster, smem_bytes, fn, am);
+    case 4: return prep_res<512, 4, 2, false>(cluster, smem_bytes, fn, am);
+    case 5: return prep_res<1024, 1, 4, true>(cluster, smem_bytes, fn, am);
+    case 6: return prep_res<1024, 2, 2, true>(cluster, smem_bytes, fn, am);
+    case 7: return prep_res<1024, 1, 8, true>(cluster, smem_bytes, fn, am);
+    case 8: return prep_res<512, 2, 4, true>(cluster, smem_bytes, fn, am);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -242,9 +357,9 @@ static void res_cfg(cudaLaunchConfig_t* cfg, cudaLaunchAttribute* at, int nt, in
   cfg->numAttrs = 1;
 }
 
-cudaError_t res_max_clusters(int variant, int cluster, size_t smem_bytes, int* out) {
+cudaError_t res_max_clusters(int variant, int cluster, size_t smem_bytes, int* out, bool async_mode) {
   void* fn = nullptr;
-  cudaError_t e = res_fn(variant, cluster, smem_bytes, &fn);
+  cudaError_t e = res_fn(variant, cluster, smem_bytes, &fn, async_mode);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute at[1];
@@ -256,6 +371,19 @@ cudaError_t launch_res_sweep(int variant, int cluster, int slots, size_t smem_by
                              cudaStream_t s) {
   void* fn = nullptr;
   cudaError_t e = res_fn(variant, cluster, smem_bytes, &fn);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute at[1];
+  res_cfg(&cfg, at, kResVariants[variant].nt, cluster, slots, smem_bytes, s);
+  const int smem_f4 = (int)(smem_bytes / 16);
+  void* args[] = {(void*)&a, (void*)&smem_f4};
+  return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+cudaError_t launch_res_async(int variant, int cluster, int slots, size_t smem_bytes, const AsyncArgs& a,
+                             cudaStream_t s) {
+  void* fn = nullptr;
+  cudaError_t e = res_fn(variant, cluster, smem_bytes, &fn, true);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute at[1];

@@ -39,7 +39,7 @@ static bool res_fits(const std::vector<Task>& tasks, int nt, int kc, int zs, int
   return true;
 }
 
-static void list_resident(Tuner& t, const std::vector<Task>& tasks, long long maxpts, int req_cluster,
+static void list_resident(Tuner& t, int mode, const std::vector<Task>& tasks, long long maxpts, int req_cluster,
                           int req_threads, int req_slots, std::vector<LaunchShape>* out) {
   const int ntasks = (int)tasks.size();
   for (int v = 0; v < res_variant_count(); ++v) {
@@ -51,13 +51,13 @@ static void list_resident(Tuner& t, const std::vector<Task>& tasks, long long ma
     for (int c = 1; c <= kMaxCluster; ++c) {
       if (req_cluster && c != req_cluster) continue;
       if (!res_fits(tasks, nt, kc, zs, c)) continue;
-      auto key = std::make_tuple(100 + v, (int)smem, nt, c);
+      auto key = std::make_tuple(100 + v + 1000 * mode, (int)smem, nt, c);
       int occ = 0;
       auto it = t.occ.find(key);
       if (it != t.occ.end()) {
         occ = it->second;
       } else {
-        if (res_max_clusters(v, c, (size_t)smem, &occ) != cudaSuccess) {
+        if (res_max_clusters(v, c, (size_t)smem, &occ, mode == 1) != cudaSuccess) {
           cudaGetLastError();
           occ = 0;
         }
@@ -122,8 +122,8 @@ std::vector<long long> signature(int prec, int mode, int engine, const std::vect
 int list_shapes(Tuner& t, int prec, int mode, int engine, const std::vector<Task>& tasks, long long maxpts,
                 int req_cluster, int req_threads, int req_slots, std::vector<LaunchShape>* out) {
   out->clear();
-  if (prec == 1 && mode == 0 && engine != 1) {
-    list_resident(t, tasks, maxpts, req_cluster, req_threads, req_slots, out);
+  if (prec == 1 && engine != 1) {
+    list_resident(t, mode, tasks, maxpts, req_cluster, req_threads, req_slots, out);
     std::stable_sort(out->begin(), out->end(),
                      [](const LaunchShape& a, const LaunchShape& b) { return a.est < b.est; });
     if (engine == 2) return out->empty() ? (int)cudaErrorInvalidConfiguration : 0;

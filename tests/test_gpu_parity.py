@@ -223,32 +223,35 @@ def test_solve_host_matches_device():
 
 
 # ---------------------------------------------------------------- asynchronous mode
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_async_converges_to_oracle_solution(prec):
+@pytest.mark.parametrize("prec,engine", [("fp64", "auto"), ("mixed", "streaming"), ("mixed", "resident")])
+def test_async_converges_to_oracle_solution(prec, engine):
     cfg = inputs.make_config("laplace32_linear")
     ref = oracle_all(cfg, **cfg["opts"])[0]
     g = make_grid(cfg["nx"], cfg["ny"], cfg["nz"], 1, cfg["cx"], cfg["cy"], cfg["cz"])
-    x, st = g.solve(bnd=cuda(cfg["bnd"]), precision=prec, mode="async", **cfg["opts"])
+    x, st = g.solve(bnd=cuda(cfg["bnd"]), precision=prec, mode="async", engine=engine, **cfg["opts"])
+    assert st.engine == (2 if engine == "resident" else 1)
     assert st.status == 0 and st.rel_residual < 1e-8
     assert g.residual(x, bnd=cuda(cfg["bnd"]))[0] < 1e-8
     assert rel_inf(x.cpu().numpy()[0], ref["x"]) <= 2 * 440 * 1e-8
 
 
-def test_async_multi_rhs_uneven():
+@pytest.mark.parametrize("engine", ["streaming", "resident"])
+def test_async_multi_rhs_uneven(engine):
     cfg = inputs.make_config("batched_uneven", scale=4)
     g = make_grid(cfg["nx"], cfg["ny"], cfg["nz"], 16, cfg["cx"], cfg["cy"], cfg["cz"])
-    x, st = g.solve(bnd=cuda(cfg["bnd"]), precision="mixed", mode="async")
+    x, st = g.solve(bnd=cuda(cfg["bnd"]), precision="mixed", mode="async", engine=engine)
     assert st.status == 0 and max(st.per_rhs_rel) < 1e-8
     assert (g.residual(x, bnd=cuda(cfg["bnd"])) < 1e-8).all()
 
 
-def test_async_tolerates_a_slow_block():
+@pytest.mark.parametrize("engine", ["streaming", "resident"])
+def test_async_tolerates_a_slow_block(engine):
     """Section 5: asynchronous block Jacobi keeps progressing when one block is slow."""
     n = 24
     c = inputs.equal_cuts(n, 2)
     bnd = inputs.boundary_uniform(n, n, n, 1, 32)
     g = make_grid(n, n, n, 1, c, c, c)
-    x, st = g.solve(bnd=cuda(bnd), precision="mixed", mode="async", slow_block=3, slow_ns=200_000)
+    x, st = g.solve(bnd=cuda(bnd), precision="mixed", mode="async", slow_block=3, slow_ns=200_000, engine=engine)
     assert st.status == 0 and st.rel_residual < 1e-8
 
 
