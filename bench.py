@@ -179,6 +179,20 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def reduce_over_ranks(total_ms, lups, device):
+    """Job-level timing over ranks: the slowest rank's time (max) and the sum of
+    every rank's lattice updates (N > 1 runs independent replicas)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1):
+        return float(total_ms), float(lups)
+    tm = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    tl = torch.tensor([float(lups)], dtype=torch.float64, device=device)
+    dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tl, op=dist.ReduceOp.SUM)
+    return float(tm.item()), float(tl.item())
+
+
 # ------------------------------------------------------------------ GPU arm
 def main():
     args = parse()
@@ -247,15 +261,7 @@ def main():
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
-    total_ms = sum(times)
-    t = torch.tensor([total_ms, float(lups)], dtype=torch.float64, device=dev)
-    if world > 1:
-        tmax = t.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        total_ms, lups_all = float(tmax[0]), float(t[1])
-    else:
-        lups_all = float(lups)
+    total_ms, lups_all = reduce_over_ranks(sum(times), lups, dev)
     value = lups_all / (total_ms * 1e-3) / 1e9
     st0 = stats[0]
 

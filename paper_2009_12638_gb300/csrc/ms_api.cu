@@ -61,6 +61,7 @@ struct Ctl {
   int err;
   int stop;
   int pad[3];
+  unsigned long long t_start;
 };
 
 }  // namespace
@@ -519,6 +520,11 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
     ca.hist = hist_dev;
     ca.outer_tol = o.outer_tol;
     ca.outer_maxit = o.outer_maxit;
+    ca.time_budget_ns = o.time_limit_ms > 0.0 ? (unsigned long long)(o.time_limit_ms * 1.0e6) : 0ull;
+    ca.t_start = &ctl->t_start;
+    ca.err = &ctl->err;
+    ca.use_cond = 0;
+    ca.cond = 0;
 
     int chunk = o.check_every > 0 ? o.check_every : 4;
     int* h_flags = nullptr;  // all_done, err
@@ -527,14 +533,6 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
       int* p;
       ~HostGuard() { cudaFreeHost(p); }
     } hg{h_flags};
-    cudaGraphExec_t gexec = nullptr;
-    int gexec_len = 0;
-    struct GraphGuard {
-      cudaGraphExec_t* e;
-      ~GraphGuard() {
-        if (*e) cudaGraphExecDestroy(*e);
-      }
-    } gg{&gexec};
     // optional per-sweep timing: one event pair per sweep of a chunk
     std::vector<cudaEvent_t> pev;
     struct EvVec {
@@ -577,7 +575,7 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
       MS_CUDA(g, cudaMemcpyAsync(h_flags, &ctl->all_done, sizeof(int), cudaMemcpyDeviceToHost, stream));
       MS_CUDA(g, cudaMemcpyAsync(h_flags + 1, &ctl->err, sizeof(int), cudaMemcpyDeviceToHost, stream));
       MS_CUDA(g, cudaStreamSynchronize(stream));
-      if (h_flags[1]) return fail(g, MS_ERR_CUDA, "ms_solve: device error word 0x%x", h_flags[1]);
+      if (h_flags[1] & kErrGeometry) return fail(g, MS_ERR_CUDA, "ms_solve: device error word 0x%x", h_flags[1]);
       float best_t = 1e30f;
       const bool verbose = std::getenv("MS_TUNE_VERBOSE") != nullptr;
       for (size_t i = 0; i < cands.size(); ++i) {
@@ -599,6 +597,62 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
       if (clean) g->tuner.best[sig] = shape;
       if (h_flags[0]) chunk = 0;  // finished during tuning
     }
+    auto sweep_launch = [&](const LaunchShape& sh, cudaStream_t cs) -> cudaError_t {
+      return sh.variant >= 0 ? launch_res_sweep(sh.variant, sh.cluster, sh.slots, sh.smem, sa, cs)
+                             : launch_sweep(prec, sh.threads, sh.cluster, sh.slots, sa, cs);
+    };
+    if (chunk != 0 && o.use_graph && !o.profile && launched <= (long long)o.outer_maxit) {
+      // The rest of the solve is ONE graph launch: a WHILE node whose body is
+      // [sweep, check]; the check kernel clears the condition on the device
+      // once every rhs has stopped (converged, outer_maxit, or time budget).
+      int k_before = 0;
+      MS_CUDA(g, cudaMemcpyAsync(&h_flags[2], &ctl->k_dev, sizeof(int), cudaMemcpyDeviceToHost, stream));
+      MS_CUDA(g, cudaStreamSynchronize(stream));
+      k_before = h_flags[2];
+      cudaGraph_t graph = nullptr;
+      cudaGraphExec_t exec = nullptr;
+      cudaError_t ce = cudaGraphCreate(&graph, 0);
+      cudaGraphConditionalHandle cond = 0;
+      if (ce == cudaSuccess) ce = cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault);
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = cond;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      cudaGraphNode_t node;
+      if (ce == cudaSuccess) ce = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+      if (ce == cudaSuccess) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        cudaStream_t cs = nullptr;
+        ce = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (ce == cudaSuccess) {
+          CheckArgs cb = ca;
+          cb.use_cond = 1;
+          cb.cond = cond;
+          ce = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+          cudaError_t c1 = ce == cudaSuccess ? sweep_launch(shape, cs) : ce;
+          cudaError_t c2 = c1 == cudaSuccess ? launch_check(cb, cs) : c1;
+          cudaError_t c3 = ce == cudaSuccess ? cudaStreamEndCapture(cs, &body) : cudaSuccess;
+          if (ce == cudaSuccess) ce = c2 != cudaSuccess ? c2 : c3;
+          cudaStreamDestroy(cs);
+        }
+      }
+      if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
+      if (ce == cudaSuccess) ce = cudaGraphLaunch(exec, stream);
+      if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_flags, &ctl->all_done, sizeof(int), cudaMemcpyDeviceToHost, stream);
+      if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_flags + 1, &ctl->err, sizeof(int), cudaMemcpyDeviceToHost, stream);
+      if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_flags + 2, &ctl->k_dev, sizeof(int), cudaMemcpyDeviceToHost, stream);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
+      if (exec) cudaGraphExecDestroy(exec);
+      if (graph) cudaGraphDestroy(graph);
+      MS_CUDA(g, ce);
+      launches += 2 * (h_flags[2] - k_before);
+      launched += h_flags[2] - k_before;
+      if (h_flags[1] & kErrGeometry) return fail(g, MS_ERR_CUDA, "ms_solve: device error word 0x%x", h_flags[1]);
+      if (h_flags[1] & kErrTimeout) status = MS_ERR_TIMEOUT;
+      chunk = 0;
+    }
+    // plain launches (graphs disabled, or per-sweep event timing requested)
     for (;;) {
       if (chunk == 0) break;
       const long long remaining = (long long)o.outer_maxit + 1 - launched;
@@ -611,44 +665,18 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
           pev.push_back(e);
         }
       }
-      auto one_sweep = [&](int i, cudaStream_t cs) -> cudaError_t {
-        cudaError_t ce = cudaSuccess;
-        if (o.profile) ce = cudaEventRecord(pev[2 * i], cs);
-        if (ce == cudaSuccess)
-          ce = shape.variant >= 0 ? launch_res_sweep(shape.variant, shape.cluster, shape.slots, shape.smem, sa, cs)
-                                  : launch_sweep(prec, shape.threads, shape.cluster, shape.slots, sa, cs);
-        if (ce == cudaSuccess && o.profile) ce = cudaEventRecord(pev[2 * i + 1], cs);
-        if (ce == cudaSuccess) ce = launch_check(ca, cs);
-        return ce;
-      };
-      // (event timing is not available from graph-recorded events: profile runs launch directly)
-      if (o.use_graph && !o.profile && n == chunk) {
-        if (!gexec || gexec_len != n) {
-          if (gexec) cudaGraphExecDestroy(gexec);
-          gexec = nullptr;
-          cudaStream_t cs;
-          MS_CUDA(g, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-          cudaGraph_t graph = nullptr;
-          cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-          for (int i = 0; i < n && ce == cudaSuccess; ++i) ce = one_sweep(i, cs);
-          cudaError_t ce2 = cudaStreamEndCapture(cs, &graph);
-          if (ce == cudaSuccess) ce = ce2;
-          if (ce == cudaSuccess) ce = cudaGraphInstantiate(&gexec, graph, 0);
-          if (graph) cudaGraphDestroy(graph);
-          cudaStreamDestroy(cs);
-          MS_CUDA(g, ce);
-          gexec_len = n;
-        }
-        MS_CUDA(g, cudaGraphLaunch(gexec, stream));
-      } else {
-        for (int i = 0; i < n; ++i) MS_CUDA(g, one_sweep(i, stream));
+      for (int i = 0; i < n; ++i) {
+        if (o.profile) MS_CUDA(g, cudaEventRecord(pev[2 * i], stream));
+        MS_CUDA(g, sweep_launch(shape, stream));
+        if (o.profile) MS_CUDA(g, cudaEventRecord(pev[2 * i + 1], stream));
+        MS_CUDA(g, launch_check(ca, stream));
       }
       launched += n;
       launches += 2 * n;
       MS_CUDA(g, cudaMemcpyAsync(h_flags, &ctl->all_done, sizeof(int), cudaMemcpyDeviceToHost, stream));
       MS_CUDA(g, cudaMemcpyAsync(h_flags + 1, &ctl->err, sizeof(int), cudaMemcpyDeviceToHost, stream));
       MS_CUDA(g, cudaStreamSynchronize(stream));
-      if (h_flags[1]) return fail(g, MS_ERR_CUDA, "ms_solve: device error word 0x%x", h_flags[1]);
+      if (h_flags[1] & kErrGeometry) return fail(g, MS_ERR_CUDA, "ms_solve: device error word 0x%x", h_flags[1]);
       if (o.profile) {
         for (int i = 0; i < n; ++i) {
           float t = 0.f;
@@ -656,6 +684,10 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
           sweep_ms += t;
           sweeps_timed += 1;
         }
+      }
+      if (h_flags[1] & kErrTimeout) {
+        status = MS_ERR_TIMEOUT;
+        break;
       }
       if (h_flags[0]) break;
       if (o.time_limit_ms > 0.0) {

@@ -71,6 +71,11 @@ struct CheckArgs {
   double* hist;  // [nrhs][outer_maxit+1] or null
   double outer_tol;
   int outer_maxit;
+  unsigned long long time_budget_ns;  // 0 = none: else active rhs stop (kErrTimeout) once spent
+  unsigned long long* t_start;        // device start time, set by the first check of the solve
+  int* err;
+  int use_cond;                       // set the WHILE condition of the enclosing graph
+  cudaGraphConditionalHandle cond;
 };
 
 // Asynchronous persistent solve (see ms_async.cu).  Task t = (block, rhs) is

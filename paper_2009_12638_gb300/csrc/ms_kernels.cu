@@ -117,6 +117,14 @@ __global__ void __launch_bounds__(NT, 1) sweep_kernel(const SweepArgs a) {
 // stop rule, bookkeeping for the next sweep.
 __global__ void check_kernel(const CheckArgs a) {
   const int k = *a.k_dev;
+  __shared__ int timed_out;
+  if (threadIdx.x == 0) {
+    unsigned long long now;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+    if (*a.t_start == 0ull) *a.t_start = now;
+    timed_out = (a.time_budget_ns && now - *a.t_start > a.time_budget_ns) ? 1 : 0;
+  }
+  __syncthreads();
   for (int s = threadIdx.x; s < a.nrhs; s += blockDim.x) {
     if (a.rhs_state[s] != kActive) continue;
     double sum = 0.0;
@@ -127,7 +135,7 @@ __global__ void check_kernel(const CheckArgs a) {
     if (rho < a.outer_tol) {
       a.rhs_state[s] = kConverged;
       a.k_final[s] = k;
-    } else if (k >= a.outer_maxit) {
+    } else if (k >= a.outer_maxit || timed_out) {
       a.rhs_state[s] = kStopped;
       a.k_final[s] = k;
     }
@@ -137,9 +145,12 @@ __global__ void check_kernel(const CheckArgs a) {
     int done = 1;
     for (int s = 0; s < a.nrhs; ++s)
       if (a.rhs_state[s] == kActive) done = 0;
+    if (timed_out) atomicOr(a.err, kErrTimeout);
     *a.all_done = done;
     *a.counter = 0u;
     *a.k_dev = k + 1;
+    // the enclosing WHILE node of a whole-solve graph runs another sweep only if work is left
+    if (a.use_cond) cudaGraphSetConditional(a.cond, done ? 0u : 1u);
   }
 }
 
