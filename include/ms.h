@@ -88,6 +88,11 @@ typedef struct {
   double* res_hist;      /* HOST, optional: [nrhs][outer_maxit+1] relative residual per sweep
                             (sync mode; entries after each rhs stops are left untouched) */
   int profile;           /* sync mode: time every sweep kernel with CUDA events (stats.sweep_ms) */
+  int persistent;        /* sync mode, resident engine: 2 = all sweeps in one persistent launch, a
+                            task starts as soon as its neighbours finished the previous sweep and
+                            that sweep's stop decision is made; 0 = one launch per sweep;
+                            1 (default) = persistent when more than 5% of the per-sweep schedule's
+                            last round would idle */
   int engine;            /* inner-CG engine: 0 auto, 1 streaming (CG vectors in a global scratch slot
                             per cluster, any block size, FP32 or FP64), 2 resident (CG vectors in
                             registers and shared memory of the cluster; MIXED + SYNC, blocks that fit) */

@@ -67,7 +67,7 @@ def _stream_handle(device):
 
 def _make_opts(lib, mode="sync", precision="mixed", inner_rtol=1e-6, inner_maxit=50, outer_tol=1e-8,
                outer_maxit=100000, time_limit_ms=0.0, cluster=0, threads=0, slots=0, check_every=0, use_graph=True,
-               slow_block=-1, slow_ns=0, profile=False, engine="auto"):
+               slow_block=-1, slow_ns=0, profile=False, engine="auto", persistent="auto"):
     o = _lib.Opts()
     lib.ms_default_opts(ctypes.byref(o))
     o.mode = _lib.MODE[mode] if isinstance(mode, str) else int(mode)
@@ -85,6 +85,8 @@ def _make_opts(lib, mode="sync", precision="mixed", inner_rtol=1e-6, inner_maxit
     o.slow_block = int(slow_block)
     o.slow_ns = int(slow_ns)
     o.profile = 1 if profile else 0
+    o.persistent = {"auto": 1, True: 2, False: 0}[persistent] if not isinstance(persistent, int) or isinstance(
+        persistent, bool) else int(persistent)
     o.engine = {"auto": 0, "streaming": 1, "resident": 2}[engine] if isinstance(engine, str) else int(engine)
     return o
 
@@ -172,7 +174,7 @@ class Grid:
         opts: mode ('sync'|'async'), precision ('mixed'|'fp64'), inner_rtol,
         inner_maxit, outer_tol, outer_maxit, time_limit_ms, cluster, threads,
         slots, check_every, use_graph, slow_block, slow_ns, profile,
-        engine ('auto'|'streaming'|'resident').
+        engine ('auto'|'streaming'|'resident'), persistent.
         """
         f = self._field(f, "f", self.shape)
         bnd = self._field(bnd, "bnd", (self.nrhs, self.nbnd))

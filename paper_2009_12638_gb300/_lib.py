@@ -48,6 +48,7 @@ class Opts(ctypes.Structure):
         ("slow_ns", ctypes.c_int),
         ("res_hist", ctypes.POINTER(ctypes.c_double)),
         ("profile", ctypes.c_int),
+        ("persistent", ctypes.c_int),
         ("engine", ctypes.c_int),
     ]
 

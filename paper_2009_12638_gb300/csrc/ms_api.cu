@@ -82,6 +82,7 @@ struct ms_grid {
   DevBuf rpart;    // residual partials
   DevBuf host_io;  // device copies for ms_solve_host: f, bnd, x
   DevBuf async_ws; // face buffers, halos, seq counters (async mode)
+  DevBuf flow_ws;  // tickets, per-task progress, per-sweep counters (persistent sync mode)
   Tuner tuner;
   long long npts() const { return (long long)nx * ny * nz; }
   long long nbnd() const { return ms_boundary_size(nx, ny, nz); }
@@ -146,6 +147,7 @@ extern "C" void ms_default_opts(ms_opts* o) {
   o->slow_ns = 0;
   o->res_hist = nullptr;
   o->profile = 0;
+  o->persistent = 1;
   o->engine = 0;
 }
 
@@ -374,6 +376,7 @@ extern "C" int ms_destroy(ms_grid* g) {
   g->rpart.release();
   g->host_io.release();
   g->async_ws.release();
+  g->flow_ws.release();
   g->tuner.release();
   delete g;
   return MS_OK;
@@ -601,6 +604,63 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
       return sh.variant >= 0 ? launch_res_sweep(sh.variant, sh.cluster, sh.slots, sh.smem, sa, cs)
                              : launch_sweep(prec, sh.threads, sh.cluster, sh.slots, sa, cs);
     };
+    // persistent launch where the per-sweep schedule would idle many clusters in its
+    // last round (tasks not a multiple of the clusters in flight), unless disabled
+    const double rounds = (double)ntasks / std::max(1, shape.slots);
+    const double tail_waste = 1.0 - rounds / std::ceil(rounds);
+    const bool use_flow = o.persistent == 1 ? tail_waste > 0.05 : o.persistent == 2;
+    if (chunk != 0 && shape.variant >= 0 && use_flow && !o.profile && launched <= (long long)o.outer_maxit) {
+      // The rest of the solve is ONE persistent launch (dataflow between sweeps).
+      MS_CUDA(g, cudaMemcpyAsync(&h_flags[2], &ctl->k_dev, sizeof(int), cudaMemcpyDeviceToHost, stream));
+      MS_CUDA(g, cudaStreamSynchronize(stream));
+      const int k0 = h_flags[2];
+      const int nblocks = g->px * g->py * g->pz;
+      std::vector<int> task_of((size_t)g->nrhs * nblocks, -1);
+      for (int i = 0; i < ntasks; ++i) task_of[(size_t)tasks[i].rhs * nblocks + tasks[i].block] = i;
+      const size_t nres = (size_t)std::max(1, o.outer_maxit + 2 - k0);
+      size_t off = 0;
+      auto take = [&](size_t bytes) {
+        const size_t r = off;
+        off += (bytes + 255) / 256 * 256;
+        return r;
+      };
+      const size_t o_ticket = take(sizeof(unsigned long long)), o_dec = take(sizeof(int));
+      const size_t o_done = take((size_t)ntasks * sizeof(int)), o_res = take(nres * sizeof(int));
+      const size_t o_tof = take(task_of.size() * sizeof(int));
+      MS_CUDA(g, g->flow_ws.reserve(off));
+      char* fw = g->flow_ws.as<char>();
+      MS_CUDA(g, cudaMemsetAsync(fw, 0, o_tof, stream));
+      MS_CUDA(g, cudaMemsetAsync(fw + o_dec, 0xFF, sizeof(int), stream));  // decided_rel = -1
+      MS_CUDA(g, cudaMemcpyAsync(fw + o_tof, task_of.data(), task_of.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                 stream));
+      FlowArgs fa;
+      fa.s = sa;
+      fa.c = ca;
+      fa.k0 = k0;
+      fa.px = g->px;
+      fa.py = g->py;
+      fa.pz = g->pz;
+      fa.nblocks = nblocks;
+      fa.task_of = reinterpret_cast<const int*>(fw + o_tof);
+      fa.ticket = reinterpret_cast<unsigned long long*>(fw + o_ticket);
+      fa.res_cnt = reinterpret_cast<int*>(fw + o_res);
+      fa.done_rel = reinterpret_cast<int*>(fw + o_done);
+      fa.decided_rel = reinterpret_cast<int*>(fw + o_dec);
+      fa.spin_limit = 1LL << 24;
+      int occ = 0;
+      MS_CUDA(g, res_flow_max_clusters(shape.variant, shape.cluster, shape.smem, &occ));
+      const int fslots = std::max(1, std::min(occ, ntasks));
+      MS_CUDA(g, launch_res_flow(shape.variant, shape.cluster, fslots, shape.smem, fa, stream));
+      MS_CUDA(g, cudaMemcpyAsync(h_flags, &ctl->all_done, sizeof(int), cudaMemcpyDeviceToHost, stream));
+      MS_CUDA(g, cudaMemcpyAsync(h_flags + 1, &ctl->err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+      MS_CUDA(g, cudaMemcpyAsync(h_flags + 2, &ctl->k_dev, sizeof(int), cudaMemcpyDeviceToHost, stream));
+      MS_CUDA(g, cudaStreamSynchronize(stream));
+      launches += 1;
+      launched += h_flags[2] - k0;
+      if (h_flags[1] & kErrGeometry) return fail(g, MS_ERR_CUDA, "ms_solve: device error word 0x%x", h_flags[1]);
+      if (h_flags[1] & kErrTimeout) status = MS_ERR_TIMEOUT;
+      chunk = 0;
+    }
     if (chunk != 0 && o.use_graph && !o.profile && launched <= (long long)o.outer_maxit) {
       // The rest of the solve is ONE graph launch: a WHILE node whose body is
       // [sweep, check]; the check kernel clears the condition on the device

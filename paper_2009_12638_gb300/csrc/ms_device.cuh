@@ -112,27 +112,49 @@ struct RedSmem {
   int m, done;                      // iterations taken, loop exit flag
 };
 
+// Sum of the block partials of rhs s over the task list, by one warp: lane l
+// adds tasks l, l+32, ... in order, then a fixed shuffle tree.  Deterministic
+// and identical wherever it runs (check kernel, persistent decision).  The
+// total is returned in every lane.
+__device__ __forceinline__ double rhs_partial_sum_warp(const Task* tasks, const double* partial, int ntasks, int s) {
+  const int lane = threadIdx.x & 31;
+  double acc = 0.0;
+  for (int t = lane; t < ntasks; t += 32)
+    if (tasks[t].rhs == s) acc += partial[t];
+  acc = warp_sum_to_lane0(acc);
+  return __shfl_sync(0xffffffffu, acc, 0);
+}
+
 // Neighbour sums of interior grid point (gx, gy, gz) of one rhs: `inner`
 // gets the neighbours inside the grid, `outer` the Dirichlet values of the
 // neighbours on the boundary, read from the packed faces (bnd may be null:
 // zero data).  bhat = f + outer is the right-hand side with section 2.1's
 // boundary values lifted into it, applied on the fly; (A x) = 6 x - inner.
-__device__ __forceinline__ void nbr_sums(const Geo& g, const double* __restrict__ x, const double* __restrict__ bnd,
-                                         int gx, int gy, int gz, long long gi, double& inner, double& outer) {
+// XL2: read x through L2 only (ld.global.cg) -- for kernels in which other
+// clusters write x while this one reads it.
+template <bool XL2 = false>
+__device__ __forceinline__ double ldx(const double* x, long long i) {
+  if constexpr (XL2) return __ldcg(x + i);
+  else return x[i];
+}
+
+template <bool XL2 = false>
+__device__ __forceinline__ void nbr_sums(const Geo& g, const double* x, const double* __restrict__ bnd, int gx,
+                                         int gy, int gz, long long gi, double& inner, double& outer) {
   const long long nxy = (long long)g.nx * g.ny;
   const long long fyz = (long long)g.nz * g.ny, fxz = (long long)g.nz * g.nx;
   double si = 0.0, so = 0.0;
-  if (gx > 0) si += x[gi - 1];
+  if (gx > 0) si += ldx<XL2>(x, gi - 1);
   else if (bnd) so += bnd[(long long)gz * g.ny + gy];
-  if (gx < g.nx - 1) si += x[gi + 1];
+  if (gx < g.nx - 1) si += ldx<XL2>(x, gi + 1);
   else if (bnd) so += bnd[fyz + (long long)gz * g.ny + gy];
-  if (gy > 0) si += x[gi - g.nx];
+  if (gy > 0) si += ldx<XL2>(x, gi - g.nx);
   else if (bnd) so += bnd[2 * fyz + (long long)gz * g.nx + gx];
-  if (gy < g.ny - 1) si += x[gi + g.nx];
+  if (gy < g.ny - 1) si += ldx<XL2>(x, gi + g.nx);
   else if (bnd) so += bnd[2 * fyz + fxz + (long long)gz * g.nx + gx];
-  if (gz > 0) si += x[gi - nxy];
+  if (gz > 0) si += ldx<XL2>(x, gi - nxy);
   else if (bnd) so += bnd[2 * fyz + 2 * fxz + (long long)gy * g.nx + gx];
-  if (gz < g.nz - 1) si += x[gi + nxy];
+  if (gz < g.nz - 1) si += ldx<XL2>(x, gi + nxy);
   else if (bnd) so += bnd[2 * fyz + 2 * fxz + nxy + (long long)gy * g.nx + gx];
   inner = si;
   outer = so;

@@ -78,6 +78,24 @@ struct CheckArgs {
   cudaGraphConditionalHandle cond;
 };
 
+// Synchronous solve as one persistent "dataflow" launch (ms_resident.cu):
+// tickets are handed out sweep-major; ticket j is task j % ntasks of sweep
+// k0 + j / ntasks.  A task runs once the stop decision of the previous
+// sweep is known and its block and the six neighbouring blocks finished the
+// previous sweep.  All counters are relative to the first sweep k0.
+struct FlowArgs {
+  SweepArgs s;
+  CheckArgs c;                   // bookkeeping of the stop decisions (hist, states, k_final)
+  int k0;                        // first sweep of this launch
+  int px, py, pz, nblocks;
+  const int* task_of;            // [nrhs][nblocks] -> task index
+  unsigned long long* ticket;    // ticket counter
+  int* res_cnt;                  // [outer_maxit + 2 - k0] residuals counted per sweep
+  int* done_rel;                 // [ntasks] sweeps completed since k0
+  int* decided_rel;              // last sweep (relative) whose stop decision is made, -1 before any
+  long long spin_limit;          // polls before a wait gives up (kErrTimeout)
+};
+
 // Asynchronous persistent solve (see ms_async.cu).  Task t = (block, rhs) is
 // owned by cluster t % nclusters for the whole launch.
 struct AsyncArgs {
@@ -145,6 +163,9 @@ void res_variant_info(int v, int* nt, int* kc, int* zs, int* ds);
 cudaError_t res_max_clusters(int variant, int cluster, size_t smem_bytes, int* out, bool async_mode);
 cudaError_t launch_res_async(int variant, int cluster, int slots, size_t smem_bytes, const AsyncArgs& a,
                              cudaStream_t s);
+cudaError_t launch_res_flow(int variant, int cluster, int slots, size_t smem_bytes, const FlowArgs& a,
+                            cudaStream_t s);
+cudaError_t res_flow_max_clusters(int variant, int cluster, size_t smem_bytes, int* out);
 cudaError_t launch_res_sweep(int variant, int cluster, int slots, size_t smem_bytes, const SweepArgs& a,
                              cudaStream_t s);
 

@@ -125,11 +125,11 @@ __global__ void check_kernel(const CheckArgs a) {
     timed_out = (a.time_budget_ns && now - *a.t_start > a.time_budget_ns) ? 1 : 0;
   }
   __syncthreads();
-  for (int s = threadIdx.x; s < a.nrhs; s += blockDim.x) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int s = warp; s < a.nrhs; s += nwarps) {  // one warp per rhs
     if (a.rhs_state[s] != kActive) continue;
-    double sum = 0.0;
-    for (int t = 0; t < a.ntasks; ++t)
-      if (a.tasks[t].rhs == s) sum += a.partial[t];
+    const double sum = rhs_partial_sum_warp(a.tasks, a.partial, a.ntasks, s);
+    if (lane != 0) continue;
     const double rho = sqrt(sum) * a.inv_bnorm[s];
     if (a.hist) a.hist[(long long)s * (a.outer_maxit + 1) + k] = rho;
     if (rho < a.outer_tol) {

@@ -300,12 +300,11 @@ def test_resident_one_sweep_close_to_oracle(case):
     assert st.inner_its == ref["inner_its"] or abs(st.inner_its - ref["inner_its"]) <= 2 * len(cx) * len(cy) * len(cz)
 
 
-@pytest.mark.parametrize("case", RES_CASES)
-def test_resident_converges_like_streaming(case, cluster=0):
+def resident_vs_streaming(case, cluster=0, persistent=True):
     nx, ny, nz, cx, cy, cz = case
     bnd = np.random.default_rng(51).uniform(-1, 1, size=(2, inputs.boundary_size(nx, ny, nz)))
     g = make_grid(nx, ny, nz, 2, cx, cy, cz)
-    xr, sr = g.solve(bnd=cuda(bnd), precision="mixed", engine="resident", cluster=cluster)
+    xr, sr = g.solve(bnd=cuda(bnd), precision="mixed", engine="resident", cluster=cluster, persistent=persistent)
     xs, ss = g.solve(bnd=cuda(bnd), precision="mixed", engine="streaming")
     assert sr.status == 0 and max(sr.per_rhs_rel) < 1e-8
     assert (g.residual(xr, bnd=cuda(bnd)) < 1e-8).all()
@@ -315,9 +314,15 @@ def test_resident_converges_like_streaming(case, cluster=0):
     assert rel_inf(xr.cpu().numpy()[1], ref["x"]) <= 2 * kappa * 1e-8
 
 
+@pytest.mark.parametrize("case", RES_CASES)
+@pytest.mark.parametrize("persistent", [True, False])
+def test_resident_converges_like_streaming(case, persistent):
+    resident_vs_streaming(case, 0, persistent)
+
+
 @pytest.mark.parametrize("cluster", [2, 4, 8, 16])
 def test_resident_cluster_sizes(cluster):
-    test_resident_converges_like_streaming(RES_CASES[0], cluster)
+    resident_vs_streaming(RES_CASES[0], cluster)
 
 
 @pytest.mark.parametrize("magnitude", [1e-30, 1e30])
@@ -334,6 +339,24 @@ def test_mixed_is_scale_invariant(magnitude, engine):
     assert s1.status == 0 and sm.status == 0 and sm.rel_residual < 1e-8
     assert abs(sm.outer_its - s1.outer_its) <= 1
     assert rel_inf(xm.cpu().numpy() / magnitude, x1.cpu().numpy()) <= 2 * 0.5 * (n + 1) ** 2 * 1e-8
+
+
+@pytest.mark.parametrize("persistent", [True, False])
+def test_resident_persistent_and_per_sweep_agree(persistent):
+    """The persistent dataflow launch runs exactly the strict-Jacobi sweeps of
+    the per-sweep launches: same sweeps, same inner iterations, same x."""
+    cfg = inputs.make_config("laplace256_u11", scale=4)
+    g = make_grid(cfg["nx"], cfg["ny"], cfg["nz"], 1, cfg["cx"], cfg["cy"], cfg["cz"])
+    b = cuda(cfg["bnd"])
+    shape = dict(cluster=4, threads=512)  # one explicit shape: no tuning sweeps in either run
+    x1, s1 = g.solve(bnd=b, precision="mixed", engine="resident", persistent=True, outer_tol=0.0, outer_maxit=25,
+                     **shape)
+    x2, s2 = g.solve(bnd=b, precision="mixed", engine="resident", persistent=False, outer_tol=0.0, outer_maxit=25,
+                     **shape)
+    assert s1.outer_its == s2.outer_its == 25 and s1.inner_its == s2.inner_its
+    np.testing.assert_array_equal(x1.cpu().numpy(), x2.cpu().numpy())
+    xc, sc = g.solve(bnd=b, precision="mixed", engine="resident", persistent=persistent, history=True)
+    assert sc.status == 0 and sc.rel_residual < 1e-8
 
 
 def test_resident_uneven_multi_rhs():
