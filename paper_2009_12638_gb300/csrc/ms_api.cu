@@ -443,11 +443,13 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
     }
   }
 
-  // workspace
-  const long long vec_stride = (maxpts + 31) / 32 * 32;
+  // workspace (vectors sized for the largest block, in the pitch-padded strip layout when larger)
+  long long padded = maxpts;
+  for (const Task& t : tasks) padded = std::max(padded, (long long)t.bz * t.by * 4 * ((t.bx + 3) / 4));
+  const long long vec_stride = (padded + 31) / 32 * 32;
   CtlLayout L = ctl_layout(g->nrhs);
   {
-    int streaming_slots = shape.variant < 0 ? shape.slots : 0;
+    int streaming_slots = shape.variant < 0 ? shape.slots : 0;  // scalar and vectorised streaming
     for (const LaunchShape& c : cands)
       if (c.variant < 0) streaming_slots = std::max(streaming_slots, c.slots);
     if (streaming_slots > 0) MS_CUDA(g, g->scratch.reserve((size_t)streaming_slots * 4 * vec_stride * esz));
@@ -561,8 +563,9 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
       } tevg{&tev};
       for (auto& e : tev) MS_CUDA(g, cudaEventCreate(&e));
       auto sweep_with = [&](const LaunchShape& sh) -> cudaError_t {
-        return sh.variant >= 0 ? launch_res_sweep(sh.variant, sh.cluster, sh.slots, sh.smem, sa, stream)
-                               : launch_sweep(prec, sh.threads, sh.cluster, sh.slots, sa, stream);
+        if (sh.variant >= 0) return launch_res_sweep(sh.variant, sh.cluster, sh.slots, sh.smem, sa, stream);
+        if (sh.variant == -2) return launch_strip_sweep(sh.threads, sh.cluster, sh.slots, sa, stream);
+        return launch_sweep(prec, sh.threads, sh.cluster, sh.slots, sa, stream);
       };
       MS_CUDA(g, sweep_with(cands[0]));
       MS_CUDA(g, launch_check(ca, stream));
@@ -601,8 +604,9 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
       if (h_flags[0]) chunk = 0;  // finished during tuning
     }
     auto sweep_launch = [&](const LaunchShape& sh, cudaStream_t cs) -> cudaError_t {
-      return sh.variant >= 0 ? launch_res_sweep(sh.variant, sh.cluster, sh.slots, sh.smem, sa, cs)
-                             : launch_sweep(prec, sh.threads, sh.cluster, sh.slots, sa, cs);
+      if (sh.variant >= 0) return launch_res_sweep(sh.variant, sh.cluster, sh.slots, sh.smem, sa, cs);
+      if (sh.variant == -2) return launch_strip_sweep(sh.threads, sh.cluster, sh.slots, sa, cs);
+      return launch_sweep(prec, sh.threads, sh.cluster, sh.slots, sa, cs);
     };
     // persistent launch where the per-sweep schedule would idle many clusters in its
     // last round (tasks not a multiple of the clusters in flight), unless disabled

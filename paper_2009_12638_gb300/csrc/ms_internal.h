@@ -166,6 +166,9 @@ cudaError_t launch_res_async(int variant, int cluster, int slots, size_t smem_by
 cudaError_t launch_res_flow(int variant, int cluster, int slots, size_t smem_bytes, const FlowArgs& a,
                             cudaStream_t s);
 cudaError_t res_flow_max_clusters(int variant, int cluster, size_t smem_bytes, int* out);
+// vectorised FP32 streaming engine, sync mode (ms_stream4.cu)
+cudaError_t strip_max_clusters(int threads, int cluster, int* out);
+cudaError_t launch_strip_sweep(int threads, int cluster, int slots, const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_res_sweep(int variant, int cluster, int slots, size_t smem_bytes, const SweepArgs& a,
                              cudaStream_t s);
 

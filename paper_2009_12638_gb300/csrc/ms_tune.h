@@ -15,7 +15,8 @@ struct LaunchShape {
   int cluster = 1;
   int threads = 512;
   int slots = 1;
-  int variant = -1;   // >= 0: resident engine variant (ms_resident.cu); -1: streaming engine
+  int variant = -1;   // >= 0: resident engine variant (ms_resident.cu); -1: streaming engine;
+                      // -2: vectorised FP32 streaming engine (ms_stream4.cu)
   size_t smem = 0;    // dynamic shared memory bytes (resident engine)
   double est = 0.0;   // model estimate used to rank shapes before measuring
 };

@@ -287,13 +287,16 @@ RES_CASES = [
 
 
 @pytest.mark.parametrize("case", RES_CASES)
-def test_resident_one_sweep_close_to_oracle(case):
+@pytest.mark.parametrize("engine,threads", [("resident", 0), ("streaming", 512), ("streaming", 1024),
+                                            ("streaming", 256)])
+def test_mixed_one_sweep_close_to_oracle(case, engine, threads):
     """One sweep from x0 = 0 is one FP32 CG solve per block: it must match the
-    FP64 oracle's sweep to FP32-CG accuracy."""
+    FP64 oracle's sweep to FP32-CG accuracy.  Streaming with 512/1024 threads
+    is the vectorised strip engine, with 256 the scalar one."""
     nx, ny, nz, cx, cy, cz = case
     bnd = np.random.default_rng(50).uniform(-1, 1, size=(1, inputs.boundary_size(nx, ny, nz)))
     g = make_grid(nx, ny, nz, 1, cx, cy, cz)
-    x, st = g.solve(bnd=cuda(bnd), precision="mixed", engine="resident", outer_tol=0.0, outer_maxit=1)
+    x, st = g.solve(bnd=cuda(bnd), precision="mixed", engine=engine, threads=threads, outer_tol=0.0, outer_maxit=1)
     ref = oracle.solve(nx, ny, nz, cx, cy, cz, bnd=bnd[0], outer_tol=0.0, outer_maxit=1)
     assert st.outer_its == 1
     assert rel_inf(x.cpu().numpy()[0], ref["x"]) <= 2e-4
