@@ -41,7 +41,8 @@ OUTER_BYTES = {"mixed": 32.0, "fp64": 40.0}
 # DRAM traffic per launch of the dominant kernel, from one ncu capture, with
 # the hash of the kernel sources it was taken on (null once they change)
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "res_sweep_laplace256_traffic.json")
-KERNEL_SOURCES = ["ms_resident.cu", "ms_resident.cuh", "ms_device.cuh", "ms_cg.cuh", "ms_internal.h"]
+KERNEL_SOURCES = ["ms_resident_kernels.cuh", "ms_resident_variants.h", "ms_resident.cuh", "ms_async.cuh", "ms_device.cuh",
+                  "ms_cg.cuh", "ms_internal.h"]
 
 
 def kernel_source_hash():

@@ -96,6 +96,8 @@ typedef struct {
   int engine;            /* inner-CG engine: 0 auto, 1 streaming (CG vectors in a global scratch slot
                             per cluster, any block size, FP32 or FP64), 2 resident (CG vectors in
                             registers and shared memory of the cluster; MIXED + SYNC, blocks that fit) */
+  int variant;           /* resident engine: -1 (default) = chosen by the autotuner; v >= 0 = row v of
+                            the variant table (ms_resident_variant), for tests and profiling */
 } ms_opts;
 
 typedef struct {
@@ -112,6 +114,8 @@ typedef struct {
   double sweep_ms;             /* with opts.profile: summed device time of the sweep kernels */
   int sweep_launches;          /* with opts.profile: sweep kernels timed */
   int engine;                  /* inner-CG engine used: 1 streaming, 2 resident */
+  int variant;                 /* launch variant used: >= 0 resident table row, -1 scalar streaming,
+                                  -2 vectorised (float4) streaming */
 } ms_stats;
 
 /* Number of doubles in one rhs's packed boundary array. */
@@ -199,6 +203,18 @@ MS_API int ms_residual_noalloc(ms_grid* grid, const double* f, const double* bnd
 
 /* Free the handle and its device workspace.  Synchronises the device work
  * the handle issued.  NULL is accepted. */
+/* Row v of the resident engine's variant table (no counterpart in the paper:
+ * the table lists the on-chip layouts of one block's CG state that the
+ * autotuner chooses from).  threads: threads per CTA; strips: 4-point x-strips
+ * a thread owns per plane; planes: z-planes a CTA holds at most; d_smem: the
+ * correction d lives in shared memory (else registers); q_regs: A p is kept
+ * in registers between the two halves of a CG iteration (one stencil per
+ * iteration instead of two, bit-identical results).  Any output pointer may
+ * be NULL.  Returns MS_OK, or MS_ERR_ARG if v is
+ * outside [0, count); *count (if non-NULL) always receives the number of
+ * rows.  Host only, no device work. */
+MS_API int ms_resident_variant(int v, int* count, int* threads, int* strips, int* planes, int* d_smem, int* q_regs);
+
 MS_API int ms_destroy(ms_grid* grid);
 
 /* Message for the last failure on this handle (or of ms_create_grid when

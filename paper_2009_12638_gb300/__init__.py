@@ -33,6 +33,23 @@ def boundary_size(nx: int, ny: int, nz: int) -> int:
     return 2 * nz * ny + 2 * nz * nx + 2 * ny * nx
 
 
+def resident_variants():
+    """Rows of the resident engine's layout table (ms_resident_variant): a list
+    of dicts with threads, strips (4-point x-strips per thread and plane),
+    planes (z-planes per CTA at most), d_smem, q_regs."""
+    lib = _lib.load()
+    n = ctypes.c_int(0)
+    lib.ms_resident_variant(-1, ctypes.byref(n), None, None, None, None, None)
+    rows = []
+    for v in range(n.value):
+        f = [ctypes.c_int(0) for _ in range(5)]
+        rc = lib.ms_resident_variant(v, None, *[ctypes.byref(x) for x in f])
+        if rc != _lib.MS_OK:
+            raise MsError(f"ms_resident_variant({v}) returned {rc}")
+        rows.append(dict(zip(("threads", "strips", "planes", "d_smem", "q_regs"), (x.value for x in f))))
+    return rows
+
+
 @dataclass
 class SolveStats:
     status: int
@@ -50,6 +67,7 @@ class SolveStats:
     sweep_ms: float = 0.0
     sweep_launches: int = 0
     engine: int = 0
+    variant: int = -1
     history: np.ndarray | None = None
 
     @property
@@ -67,7 +85,7 @@ def _stream_handle(device):
 
 def _make_opts(lib, mode="sync", precision="mixed", inner_rtol=1e-6, inner_maxit=50, outer_tol=1e-8,
                outer_maxit=100000, time_limit_ms=0.0, cluster=0, threads=0, slots=0, check_every=0, use_graph=True,
-               slow_block=-1, slow_ns=0, profile=False, engine="auto", persistent="auto"):
+               slow_block=-1, slow_ns=0, profile=False, engine="auto", persistent="auto", variant=-1):
     o = _lib.Opts()
     lib.ms_default_opts(ctypes.byref(o))
     o.mode = _lib.MODE[mode] if isinstance(mode, str) else int(mode)
@@ -88,6 +106,7 @@ def _make_opts(lib, mode="sync", precision="mixed", inner_rtol=1e-6, inner_maxit
     o.persistent = {"auto": 1, True: 2, False: 0}[persistent] if not isinstance(persistent, int) or isinstance(
         persistent, bool) else int(persistent)
     o.engine = {"auto": 0, "streaming": 1, "resident": 2}[engine] if isinstance(engine, str) else int(engine)
+    o.variant = int(variant)
     return o
 
 
@@ -174,7 +193,8 @@ class Grid:
         opts: mode ('sync'|'async'), precision ('mixed'|'fp64'), inner_rtol,
         inner_maxit, outer_tol, outer_maxit, time_limit_ms, cluster, threads,
         slots, check_every, use_graph, slow_block, slow_ns, profile,
-        engine ('auto'|'streaming'|'resident'), persistent.
+        engine ('auto'|'streaming'|'resident'), persistent, variant (resident
+        layout row, see resident_variants(); -1 = tuned).
         """
         f = self._field(f, "f", self.shape)
         bnd = self._field(bnd, "bnd", (self.nrhs, self.nbnd))
@@ -204,7 +224,7 @@ class Grid:
             self._check(rc)
         stats = SolveStats(rc, st.outer_its, st.inner_its, st.lups, st.rel_residual, st.time_ms, st.launches,
                            st.cluster, st.threads, st.slots, list(per_its), list(per_rel), st.sweep_ms,
-                           st.sweep_launches, st.engine)
+                           st.sweep_launches, st.engine, st.variant)
         if hist is not None:
             stats.history = hist
         return out, stats
@@ -233,7 +253,8 @@ class Grid:
         if rc not in (_lib.MS_OK, _lib.MS_ERR_NOT_CONVERGED, _lib.MS_ERR_TIMEOUT):
             self._check(rc)
         return x, SolveStats(rc, st.outer_its, st.inner_its, st.lups, st.rel_residual, st.time_ms, st.launches,
-                             st.cluster, st.threads, st.slots, [], [])
+                             st.cluster, st.threads, st.slots, [], [], st.sweep_ms, st.sweep_launches, st.engine,
+                             st.variant)
 
     def residual(self, x, f=None, bnd=None):
         """True relative residual per rhs (absolute where ||bhat|| = 0), computed on the GPU."""

@@ -26,7 +26,7 @@ PRECISION = {"fp64": 0, "mixed": 1}
 # Symbols declared in include/ms.h (checked by the CPU tests).
 EXPORTS = ("ms_boundary_size", "ms_default_opts", "ms_create_grid", "ms_partition", "ms_get_cuts", "ms_solve",
            "ms_solve_host", "ms_residual", "ms_face_gather", "ms_destroy", "ms_last_error",
-           "ms_residual_noalloc")
+           "ms_residual_noalloc", "ms_resident_variant")
 NOALLOC_MAX_RHS = 1024
 
 
@@ -50,6 +50,7 @@ class Opts(ctypes.Structure):
         ("profile", ctypes.c_int),
         ("persistent", ctypes.c_int),
         ("engine", ctypes.c_int),
+        ("variant", ctypes.c_int),
     ]
 
 
@@ -70,6 +71,7 @@ class Stats(ctypes.Structure):
         ("sweep_ms", ctypes.c_double),
         ("sweep_launches", ctypes.c_int),
         ("engine", ctypes.c_int),
+        ("variant", ctypes.c_int),
     ]
 
 
@@ -100,6 +102,7 @@ def load(path: str = LIB_PATH):
         lib.ms_residual.argtypes = [vp, vp, vp, vp, dp, vp]
         lib.ms_face_gather.argtypes = [vp, vp, vp, vp]
         lib.ms_residual_noalloc.argtypes = [vp, vp, vp, vp, vp, vp]
+        lib.ms_resident_variant.argtypes = [c_int, ip, ip, ip, ip, ip, ip]
         lib.ms_destroy.argtypes = [vp]
         lib.ms_last_error.argtypes = [vp]
         lib.ms_last_error.restype = ctypes.c_char_p

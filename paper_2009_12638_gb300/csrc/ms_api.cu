@@ -25,6 +25,8 @@ namespace {
 
 thread_local std::string g_create_error;
 
+constexpr size_t kTuneRounds = 2;  // timed sweeps per autotuning candidate
+
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
@@ -149,6 +151,7 @@ extern "C" void ms_default_opts(ms_opts* o) {
   o->profile = 0;
   o->persistent = 1;
   o->engine = 0;
+  o->variant = -1;
 }
 
 static std::vector<int> equal_cuts(int n, int p) {
@@ -256,6 +259,10 @@ static int check_opts(ms_grid* g, const ms_opts& o) {
   if (o.slots < 0 || o.check_every < 0) return fail(g, MS_ERR_ARG, "opts.slots and opts.check_every must be >= 0");
   if (o.time_limit_ms < 0.0) return fail(g, MS_ERR_ARG, "opts.time_limit_ms must be >= 0");
   if (o.engine < 0 || o.engine > 2) return fail(g, MS_ERR_ARG, "opts.engine must be 0 (auto), 1 or 2");
+  if (o.variant < -1 || o.variant >= ms::res_variant_count())
+    return fail(g, MS_ERR_ARG, "opts.variant must be -1 (tuned) or 0..%d", ms::res_variant_count() - 1);
+  if (o.variant >= 0 && (o.precision != MS_PREC_MIXED || o.engine == 1))
+    return fail(g, MS_ERR_ARG, "opts.variant selects a resident-engine layout: it needs precision MIXED and engine 0 or 2");
   return MS_OK;
 }
 
@@ -364,6 +371,21 @@ extern "C" int ms_face_gather(ms_grid* g, const double* lam, double* grad_bnd, v
   return MS_OK;
 }
 
+extern "C" int ms_resident_variant(int v, int* count, int* threads, int* strips, int* planes, int* d_smem,
+                                   int* q_regs) {
+  const int n = ms::res_variant_count();
+  if (count) *count = n;
+  if (v < 0 || v >= n) return MS_ERR_ARG;
+  int nt, kc, zs, ds, qr;
+  ms::res_variant_info(v, &nt, &kc, &zs, &ds, &qr);
+  if (threads) *threads = nt;
+  if (strips) *strips = kc;
+  if (planes) *planes = zs;
+  if (d_smem) *d_smem = ds;
+  if (q_regs) *q_regs = qr;
+  return MS_OK;
+}
+
 extern "C" int ms_destroy(ms_grid* g) {
   if (!g) return MS_OK;
   cudaDeviceSynchronize();
@@ -416,21 +438,22 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
   // launch shape: an explicit request, a shape measured earlier for this
   // problem, or -- sync mode -- candidates measured on the first sweeps
   std::vector<LaunchShape> all;
-  int rc = list_shapes(g->tuner, prec, o.mode, o.engine, tasks, maxpts, o.cluster, o.threads, o.slots, &all);
+  int rc = list_shapes(g->tuner, prec, o.mode, o.variant >= 0 ? 2 : o.engine, tasks, maxpts, o.cluster, o.threads,
+                       o.slots, o.variant, &all);
   if (rc != 0) return fail(g, MS_ERR_CUDA, "ms_solve: no launchable shape (%s)", cudaGetErrorString((cudaError_t)rc));
   LaunchShape shape = all.front();
   std::vector<LaunchShape> cands;
   const std::vector<long long> sig = signature(prec, o.mode, o.engine, tasks);
   {
     auto it = g->tuner.best.find(sig);
-    const bool requested = o.cluster || o.threads || o.slots;
+    const bool requested = o.cluster || o.threads || o.slots || o.variant >= 0;
     if (!requested && it != g->tuner.best.end()) {
       shape = it->second;
     } else if (!requested && o.mode == MS_MODE_SYNC) {
       int nres = 0;
       bool have_streaming = false;
       for (const LaunchShape& c : all) {
-        if (c.variant >= 0 && nres < 5) {
+        if (c.variant >= 0 && nres < 6) {
           cands.push_back(c);
           ++nres;
         } else if (c.variant < 0 && (!have_streaming || prec == 0)) {
@@ -438,8 +461,9 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
           have_streaming = true;
         }
       }
-      // sweep 0 (heuristic shape) + one sweep per candidate must fit in the sweep budget
-      if (cands.size() < 2 || (long long)o.outer_maxit < 2 * (long long)cands.size()) cands.clear();
+      // sweep 0 (heuristic shape) + kTuneRounds sweeps per candidate must fit in the sweep budget
+      if (cands.size() < 2 || (long long)o.outer_maxit < 2 * (long long)(kTuneRounds * cands.size() + 1))
+        cands.clear();
     }
   }
 
@@ -552,8 +576,11 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
     long long launched = 0;  // sweeps launched
     if (!cands.empty()) {
       // autotuning: sweep 0 with the model's favourite (x^0 leaves some blocks
-      // trivial), then one real sweep per candidate timed with CUDA events
-      std::vector<cudaEvent_t> tev(2 * cands.size());
+      // trivial), then kTuneRounds rounds of one real sweep per candidate,
+      // timed with CUDA events; a candidate's time is its fastest sweep (one
+      // sweep alone can be distorted, e.g. by the previous candidate's tail)
+      const size_t nc = cands.size();
+      std::vector<cudaEvent_t> tev(2 * kTuneRounds * nc);
       struct TevGuard {
         std::vector<cudaEvent_t>* v;
         ~TevGuard() {
@@ -569,14 +596,14 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
       };
       MS_CUDA(g, sweep_with(cands[0]));
       MS_CUDA(g, launch_check(ca, stream));
-      for (size_t i = 0; i < cands.size(); ++i) {
-        MS_CUDA(g, cudaEventRecord(tev[2 * i], stream));
-        MS_CUDA(g, sweep_with(cands[i]));
-        MS_CUDA(g, cudaEventRecord(tev[2 * i + 1], stream));
+      for (size_t j = 0; j < kTuneRounds * nc; ++j) {
+        MS_CUDA(g, cudaEventRecord(tev[2 * j], stream));
+        MS_CUDA(g, sweep_with(cands[j % nc]));
+        MS_CUDA(g, cudaEventRecord(tev[2 * j + 1], stream));
         MS_CUDA(g, launch_check(ca, stream));
       }
-      launched += 1 + (long long)cands.size();
-      launches += 2 * (1 + (int)cands.size());
+      launched += 1 + (long long)(kTuneRounds * nc);
+      launches += 2 * (1 + (int)(kTuneRounds * nc));
       MS_CUDA(g, cudaMemcpyAsync(h_state.data(), rhs_state, g->nrhs * sizeof(int), cudaMemcpyDeviceToHost, stream));
       MS_CUDA(g, cudaMemcpyAsync(h_flags, &ctl->all_done, sizeof(int), cudaMemcpyDeviceToHost, stream));
       MS_CUDA(g, cudaMemcpyAsync(h_flags + 1, &ctl->err, sizeof(int), cudaMemcpyDeviceToHost, stream));
@@ -584,9 +611,13 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
       if (h_flags[1] & kErrGeometry) return fail(g, MS_ERR_CUDA, "ms_solve: device error word 0x%x", h_flags[1]);
       float best_t = 1e30f;
       const bool verbose = std::getenv("MS_TUNE_VERBOSE") != nullptr;
-      for (size_t i = 0; i < cands.size(); ++i) {
-        float t = 0.f;
-        MS_CUDA(g, cudaEventElapsedTime(&t, tev[2 * i], tev[2 * i + 1]));
+      for (size_t i = 0; i < nc; ++i) {
+        float t = 1e30f;
+        for (size_t rnd = 0; rnd < kTuneRounds; ++rnd) {
+          float tr = 0.f;
+          MS_CUDA(g, cudaEventElapsedTime(&tr, tev[2 * (rnd * nc + i)], tev[2 * (rnd * nc + i) + 1]));
+          t = std::min(t, tr);
+        }
         if (verbose)
           std::fprintf(stderr, "ms tune: variant %d cluster %d threads %d slots %d smem %zu est %.3g -> %.3f ms\n",
                        cands[i].variant, cands[i].cluster, cands[i].threads, cands[i].slots, cands[i].smem,
@@ -608,11 +639,42 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
       if (sh.variant == -2) return launch_strip_sweep(sh.threads, sh.cluster, sh.slots, sa, cs);
       return launch_sweep(prec, sh.threads, sh.cluster, sh.slots, sa, cs);
     };
-    // persistent launch where the per-sweep schedule would idle many clusters in its
-    // last round (tasks not a multiple of the clusters in flight), unless disabled
+    // Persistent dataflow launch or per-sweep graph.  In auto mode the
+    // persistent launch is a candidate where the per-sweep schedule would idle
+    // clusters in its last round (tasks not a multiple of the clusters in
+    // flight); which of the two is faster depends on the variant (the
+    // persistent kernel holds more state), so the first solve of a problem
+    // runs the persistent launch, the next one the graph, each timed, and
+    // later solves take the faster.
     const double rounds = (double)ntasks / std::max(1, shape.slots);
     const double tail_waste = 1.0 - rounds / std::ceil(rounds);
-    const bool use_flow = o.persistent == 1 ? tail_waste > 0.05 : o.persistent == 2;
+    std::vector<long long> mode_key = sig;
+    mode_key.insert(mode_key.end(), {shape.variant, shape.cluster, shape.threads, shape.slots});
+    Tuner::ModeMs* mm = nullptr;
+    bool use_flow = o.persistent == 2;
+    if (o.persistent == 1 && shape.variant >= 0 && tail_waste > 0.05) {
+      mm = &g->tuner.mode_ms[mode_key];
+      use_flow = mm->flow < 0.0 || (mm->sweep >= 0.0 && mm->flow < mm->sweep);
+    }
+    struct PhaseEvGuard {
+      cudaEvent_t a = nullptr, b = nullptr;
+      ~PhaseEvGuard() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+      }
+    } pguard;  // timing of the main phase (auto mode choice)
+    if (mm) {
+      MS_CUDA(g, cudaEventCreate(&pguard.a));
+      MS_CUDA(g, cudaEventCreate(&pguard.b));
+    }
+    const cudaEvent_t pa = pguard.a, pb = pguard.b;
+    auto record_phase = [&](double Tuner::ModeMs::*field, long long sweeps) -> cudaError_t {
+      if (!mm || sweeps < 10 || status != MS_OK) return cudaSuccess;
+      float t = 0.f;
+      cudaError_t e = cudaEventElapsedTime(&t, pa, pb);
+      if (e == cudaSuccess) (*mm).*field = (double)t / (double)sweeps;
+      return e;
+    };
     if (chunk != 0 && shape.variant >= 0 && use_flow && !o.profile && launched <= (long long)o.outer_maxit) {
       // The rest of the solve is ONE persistent launch (dataflow between sweeps).
       MS_CUDA(g, cudaMemcpyAsync(&h_flags[2], &ctl->k_dev, sizeof(int), cudaMemcpyDeviceToHost, stream));
@@ -654,7 +716,9 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
       int occ = 0;
       MS_CUDA(g, res_flow_max_clusters(shape.variant, shape.cluster, shape.smem, &occ));
       const int fslots = std::max(1, std::min(occ, ntasks));
+      if (pa) MS_CUDA(g, cudaEventRecord(pa, stream));
       MS_CUDA(g, launch_res_flow(shape.variant, shape.cluster, fslots, shape.smem, fa, stream));
+      if (pb) MS_CUDA(g, cudaEventRecord(pb, stream));
       MS_CUDA(g, cudaMemcpyAsync(h_flags, &ctl->all_done, sizeof(int), cudaMemcpyDeviceToHost, stream));
       MS_CUDA(g, cudaMemcpyAsync(h_flags + 1, &ctl->err, sizeof(int), cudaMemcpyDeviceToHost, stream));
       MS_CUDA(g, cudaMemcpyAsync(h_flags + 2, &ctl->k_dev, sizeof(int), cudaMemcpyDeviceToHost, stream));
@@ -663,6 +727,7 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
       launched += h_flags[2] - k0;
       if (h_flags[1] & kErrGeometry) return fail(g, MS_ERR_CUDA, "ms_solve: device error word 0x%x", h_flags[1]);
       if (h_flags[1] & kErrTimeout) status = MS_ERR_TIMEOUT;
+      MS_CUDA(g, record_phase(&Tuner::ModeMs::flow, h_flags[2] - k0));
       chunk = 0;
     }
     if (chunk != 0 && o.use_graph && !o.profile && launched <= (long long)o.outer_maxit) {
@@ -702,7 +767,9 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
         }
       }
       if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
+      if (ce == cudaSuccess && pa) ce = cudaEventRecord(pa, stream);
       if (ce == cudaSuccess) ce = cudaGraphLaunch(exec, stream);
+      if (ce == cudaSuccess && pb) ce = cudaEventRecord(pb, stream);
       if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_flags, &ctl->all_done, sizeof(int), cudaMemcpyDeviceToHost, stream);
       if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_flags + 1, &ctl->err, sizeof(int), cudaMemcpyDeviceToHost, stream);
       if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_flags + 2, &ctl->k_dev, sizeof(int), cudaMemcpyDeviceToHost, stream);
@@ -714,6 +781,7 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
       launched += h_flags[2] - k_before;
       if (h_flags[1] & kErrGeometry) return fail(g, MS_ERR_CUDA, "ms_solve: device error word 0x%x", h_flags[1]);
       if (h_flags[1] & kErrTimeout) status = MS_ERR_TIMEOUT;
+      MS_CUDA(g, record_phase(&Tuner::ModeMs::sweep, h_flags[2] - k_before));
       chunk = 0;
     }
     // plain launches (graphs disabled, or per-sweep event timing requested)
@@ -834,6 +902,7 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
     st->threads = shape.threads;
     st->slots = shape.slots;
     st->engine = shape.variant >= 0 ? 2 : 1;
+    st->variant = shape.variant;
   }
   return status;
 }

@@ -159,7 +159,7 @@ cudaError_t launch_async_init(const AsyncArgs& a, cudaStream_t s);
 cudaError_t launch_async_rearm(const AsyncArgs& a, cudaStream_t s);
 // on-chip (resident) FP32 inner CG, sync mode (ms_resident.cu)
 int res_variant_count();
-void res_variant_info(int v, int* nt, int* kc, int* zs, int* ds);
+void res_variant_info(int v, int* nt, int* kc, int* zs, int* ds, int* qr);
 cudaError_t res_max_clusters(int variant, int cluster, size_t smem_bytes, int* out, bool async_mode);
 cudaError_t launch_res_async(int variant, int cluster, int slots, size_t smem_bytes, const AsyncArgs& a,
                              cudaStream_t s);

@@ -21,9 +21,11 @@
 // Per CG iteration: pass A (stencil from shared memory, eta = p.q), cluster
 // sum, pass B (stencil again, d += alpha p, r -= alpha q, gamma = r.r, r
 // halo push), cluster sum, pass C (p = r + beta p on own and halo planes).
+
 #pragma once
 #include "ms_cg.cuh"
 #include "ms_device.cuh"
+#include "ms_resident_variants.h"
 
 namespace ms {
 
@@ -34,7 +36,6 @@ struct ResGeo {
   int rp;       // smem row pitch in floats: 4 zero floats + 4*spr (the next row's zeros pad the right end)
   int ps;       // smem plane stride in floats: (by + 2) * rp
   int z0, nzs;  // own planes
-  unsigned spr_magic;  // ceil(2^32 / spr): st / spr == __umulhi(st, spr_magic) for st < 2^15
 };
 
 __device__ __forceinline__ ResGeo make_res_geo(int bx, int by, int bz, unsigned rank, unsigned csize) {
@@ -46,19 +47,9 @@ __device__ __forceinline__ ResGeo make_res_geo(int bx, int by, int bz, unsigned 
   g.nstrips = g.spr * by;
   g.rp = 4 * g.spr + 4;
   g.ps = (by + 2) * g.rp + 4;
-  g.spr_magic = (unsigned)((0x100000000ULL + (unsigned long long)g.spr - 1) / (unsigned long long)g.spr);
   g.z0 = (int)(((long long)bz * rank) / csize);
   g.nzs = (int)(((long long)bz * (rank + 1)) / csize) - g.z0;
   return g;
-}
-
-// floats of dynamic shared memory: p (zs + 2 planes), 2 r-halo planes, and
-// (d_in_smem) d as zs compact planes of 4*spr*by floats.
-__host__ __device__ inline long long res_smem_floats(int bx, int by, int zs, bool d_in_smem) {
-  const long long spr = (bx + 3) / 4;
-  const long long rp = 4 * spr + 4;
-  const long long ps = (by + 2) * rp + 4;  // + the right pad of the last row
-  return (zs + 4) * ps + (d_in_smem ? zs * 4 * spr * by : 0);
 }
 
 __device__ __forceinline__ void st_cluster_v4(float* local, unsigned rank, float4 v) {
@@ -94,9 +85,15 @@ __device__ __forceinline__ float cluster_sum_f32(float v, float* slots, unsigned
   v = __shfl_sync(0xffffffffu, v, 0);
   if (lane < (int)csize) st_cluster_f32(&slots[rank * NW + warp], (unsigned)lane, v);
   cl_barrier();
+  // csize * NW slots, NW a multiple of 4: float4 loads, lane l takes float4s l, l + 32, ...
+  static_assert(NW % 4 == 0, "slots are summed as float4");
+  const float4* s4 = reinterpret_cast<const float4*>(slots);
+  const int n4 = (int)csize * (NW / 4);
   float acc = 0.f;
-  const int n = (int)csize * NW;
-  for (int i = lane; i < n; i += 32) acc += slots[i];
+  for (int i = lane; i < n4; i += 32) {
+    const float4 w = s4[i];
+    acc += (w.x + w.y) + (w.z + w.w);
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   return __shfl_sync(0xffffffffu, acc, 0);
@@ -160,8 +157,8 @@ __device__ __forceinline__ Strips<KC> make_strips(const ResGeo& g) {
 
 // Reduction slots of the resident engine (FP32, one per warp per CTA).
 struct ResRed {
-  float eta[kMaxCluster * 32];
-  float gam[kMaxCluster * 32];
+  __align__(16) float eta[kMaxCluster * 32];
+  __align__(16) float gam[kMaxCluster * 32];
 };
 
 // Inner CG on the resident state.  On entry r4 holds r (padding lanes 0),
@@ -177,7 +174,12 @@ __device__ __forceinline__ float4* d_slot(float* sp, const ResGeo& g, int z, int
   return reinterpret_cast<float4*>(sp + (long long)(ZS + 4) * g.ps) + (long long)z * g.nstrips + st;
 }
 
-template <int NT, int KC, int ZS, bool DS>
+// QR: q = A_ii p of pass A stays in registers for pass B (no second stencil),
+// and the update d += alpha p moves to the next pass C, which reads p_old
+// anyway (the last one runs after the loop).  The FMAs and their order are
+// those of the QR = false path, so both give bit-identical results; QR costs
+// 4 registers per strip-plane and saves pass B's shared-memory reads.
+template <int NT, int KC, int ZS, bool DS, bool QR>
 __device__ int resident_cg(float4 (&r4)[KC][ZS], float4 (&d4)[DS ? 1 : KC][DS ? 1 : ZS], const ResGeo& g,
                            const Strips<KC>& s,
                            float* sp, float gamma0, float inner_rtol, int inner_maxit, ResRed& rr, unsigned rank,
@@ -187,11 +189,27 @@ __device__ int resident_cg(float4 (&r4)[KC][ZS], float4 (&d4)[DS ? 1 : KC][DS ? 
   float* p_lo = sp;                                // p halo plane below (plane 0)
   float* p_hi = sp + (long long)(g.nzs + 1) * g.ps;
   const bool has_lo = rank > 0, has_hi = rank + 1 < csize;
-  const int tid = threadIdx.x;
   if (!(gamma0 > 0.f) || inner_maxit <= 0) return 0;
   const float stop = inner_rtol * sqrtf(gamma0);
-  float gamma = gamma0, beta = 0.f;
+  float gamma = gamma0, beta = 0.f, alpha = 0.f;
+  float4 q4[QR ? KC : 1][QR ? ZS : 1];
   int m = 0;
+  // d = alpha p + d on one strip-plane (d = alpha p when first == true)
+  auto add_d = [&](int k, int z, float4 p, bool first) {
+    if constexpr (DS) {
+      float4* dp = d_slot<NT, KC, ZS, DS>(sp, g, z, s.st[k]);
+      const float4 d = first ? make_float4(0.f, 0.f, 0.f, 0.f) : *dp;
+      *dp = make_float4(fmaf(alpha, p.x, d.x), fmaf(alpha, p.y, d.y), fmaf(alpha, p.z, d.z), fmaf(alpha, p.w, d.w));
+    } else {
+      const float4 d = first ? make_float4(0.f, 0.f, 0.f, 0.f) : d4[k][z];
+      d4[k][z] = make_float4(fmaf(alpha, p.x, d.x), fmaf(alpha, p.y, d.y), fmaf(alpha, p.z, d.z),
+                             fmaf(alpha, p.w, d.w));
+    }
+  };
+  auto axpy4 = [](float a, float4 x, float4 y) {  // a x + y, per component
+    return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+  };
+  bool pending = false;  // QR: alpha p of the last iteration is not in d yet
   for (;;) {
     // ---------------- pass C: p = r + beta p on own planes and both halo planes
     // (beta = 0 on entry: p = r, halo p = neighbours' r; p planes start zeroed)
@@ -203,25 +221,21 @@ __device__ int resident_cg(float4 (&r4)[KC][ZS], float4 (&d4)[DS ? 1 : KC][DS ? 
         if (z >= g.nzs) break;
         float* pp = sp + (long long)(z + 1) * g.ps + s.off[k];
         const float4 po = lds4(pp);
-        const float4 r = r4[k][z];
-        sts4(pp, make_float4(fmaf(beta, po.x, r.x), fmaf(beta, po.y, r.y), fmaf(beta, po.z, r.z),
-                             fmaf(beta, po.w, r.w)));
+        if constexpr (QR) {
+          if (m > 0) add_d(k, z, po, m == 1);
+        }
+        sts4(pp, axpy4(beta, po, r4[k][z]));
       }
     }
-    // halo planes: every strip of the plane, thread-strided (y = st / spr by multiply-high)
-    for (int st = tid; st < g.nstrips; st += NT) {
-      const int y = (int)__umulhi((unsigned)st, g.spr_magic), xs = st - y * g.spr;
-      const int o = (y + 1) * g.rp + 4 + 4 * xs;
-      if (has_lo) {
-        const float4 po = lds4(p_lo + o), r = lds4(rh_lo + o);
-        sts4(p_lo + o, make_float4(fmaf(beta, po.x, r.x), fmaf(beta, po.y, r.y), fmaf(beta, po.z, r.z),
-                                   fmaf(beta, po.w, r.w)));
-      }
-      if (has_hi) {
-        const float4 po = lds4(p_hi + o), r = lds4(rh_hi + o);
-        sts4(p_hi + o, make_float4(fmaf(beta, po.x, r.x), fmaf(beta, po.y, r.y), fmaf(beta, po.z, r.z),
-                                   fmaf(beta, po.w, r.w)));
-      }
+    pending = false;
+    // halo planes: the thread's own strips (strip tid + k NT sits at the same
+    // offset in every plane), which cover every strip of a plane
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+      if (!s.msk[k]) continue;
+      const int o = s.off[k];
+      if (has_lo) sts4(p_lo + o, axpy4(beta, lds4(p_lo + o), lds4(rh_lo + o)));
+      if (has_hi) sts4(p_hi + o, axpy4(beta, lds4(p_hi + o), lds4(rh_hi + o)));
     }
     __syncthreads();
     // ---------------- pass A: q = A_ii p, eta = p.q
@@ -238,6 +252,7 @@ __device__ int resident_cg(float4 (&r4)[KC][ZS], float4 (&d4)[DS ? 1 : KC][DS ? 
         const float* cp = base + (long long)(z + 1) * g.ps;
         const float4 zp = lds4(cp + g.ps);
         const float4 q = mask4(stencil4(cp, g.rp, c, zm, zp, lft, rgt), s.msk[k]);
+        if constexpr (QR) q4[k][z] = q;
         eta_loc += dot4(c, q);
         zm = c;
         c = zp;
@@ -245,52 +260,64 @@ __device__ int resident_cg(float4 (&r4)[KC][ZS], float4 (&d4)[DS ? 1 : KC][DS ? 
     }
     const float eta = cluster_sum_f32<NT>(eta_loc, rr.eta, rank, csize);
     if (!(eta > 0.f)) break;  // curvature breakdown or NaN: keep d from earlier steps
-    const float alpha = gamma / eta;
-    // ---------------- pass B: d += alpha p, r -= alpha q, gamma = r.r, push boundary r
+    alpha = gamma / eta;
+    // ---------------- pass B: (QR = false: d += alpha p,) r -= alpha q, gamma = r.r, push boundary r
     float g_loc = 0.f;
 #pragma unroll
     for (int k = 0; k < KC; ++k) {
       const float* base = sp + s.off[k];
       const bool lft = s.nb[k] & 1u, rgt = s.nb[k] & 2u;
-      float4 zm = lds4(base);
-      float4 c = lds4(base + g.ps);
+      float4 zm, c;
+      if constexpr (!QR) {
+        zm = lds4(base);
+        c = lds4(base + g.ps);
+      }
 #pragma unroll
       for (int z = 0; z < ZS; ++z) {
         if (z >= g.nzs) break;
-        const float* cp = base + (long long)(z + 1) * g.ps;
-        const float4 zp = lds4(cp + g.ps);
-        const float4 q = mask4(stencil4(cp, g.rp, c, zm, zp, lft, rgt), s.msk[k]);
-        if constexpr (DS) {
-          if (s.msk[k]) {
-            float4* dp = d_slot<NT, KC, ZS, DS>(sp, g, z, s.st[k]);
-            const float4 d = (m == 0) ? make_float4(0.f, 0.f, 0.f, 0.f) : *dp;
-            *dp = make_float4(fmaf(alpha, c.x, d.x), fmaf(alpha, c.y, d.y), fmaf(alpha, c.z, d.z),
-                              fmaf(alpha, c.w, d.w));
-          }
+        float4 q;
+        if constexpr (QR) {
+          q = q4[k][z];
         } else {
-          float4 d = d4[k][z];
-          if (m == 0) d = make_float4(0.f, 0.f, 0.f, 0.f);
-          d4[k][z] = make_float4(fmaf(alpha, c.x, d.x), fmaf(alpha, c.y, d.y), fmaf(alpha, c.z, d.z),
-                                 fmaf(alpha, c.w, d.w));
+          const float* cp = base + (long long)(z + 1) * g.ps;
+          const float4 zp = lds4(cp + g.ps);
+          q = mask4(stencil4(cp, g.rp, c, zm, zp, lft, rgt), s.msk[k]);
+          if (DS ? (s.msk[k] != 0u) : true) add_d(k, z, c, m == 0);
+          zm = c;
+          c = zp;
         }
-        float4 r = r4[k][z];
-        r = make_float4(fmaf(-alpha, q.x, r.x), fmaf(-alpha, q.y, r.y), fmaf(-alpha, q.z, r.z),
-                        fmaf(-alpha, q.w, r.w));
+        const float4 r = axpy4(-alpha, q, r4[k][z]);
         r4[k][z] = r;
         g_loc += dot4(r, r);
         if (s.msk[k]) {
           if (z == 0 && has_lo) st_cluster_v4(rh_hi + s.off[k], rank - 1, r);
           if (z == g.nzs - 1 && has_hi) st_cluster_v4(rh_lo + s.off[k], rank + 1, r);
         }
-        zm = c;
-        c = zp;
       }
     }
+    pending = QR;
     const float gnew = cluster_sum_f32<NT>(g_loc, rr.gam, rank, csize);
     m += 1;
     if (sqrtf(gnew) <= stop || m >= inner_maxit) break;
     beta = gnew / gamma;
     gamma = gnew;
+  }
+  if constexpr (QR) {
+    // the last d += alpha p (own strips only: p was written by this thread)
+    if (pending) {
+#pragma unroll
+      for (int k = 0; k < KC; ++k) {
+        if (!s.msk[k]) continue;
+#pragma unroll
+        for (int z = 0; z < ZS; ++z) {
+          if (z >= g.nzs) break;
+          add_d(k, z, lds4(sp + (long long)(z + 1) * g.ps + s.off[k]), m == 1);
+        }
+      }
+    }
+    // callers clear shared memory for the next task as soon as this returns:
+    // no thread may do so while another is still reading its p above
+    __syncthreads();
   }
   return m;
 }

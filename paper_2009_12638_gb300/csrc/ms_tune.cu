@@ -1,6 +1,7 @@
 // ms_tune.cu -- launch-shape heuristics (see ms_tune.h).
 #include <algorithm>
 
+#include "ms_resident_variants.h"
 #include "ms_tune.h"
 
 namespace ms {
@@ -21,11 +22,7 @@ static int max_clusters(Tuner& t, int prec, int mode, int threads, int cluster, 
 
 static long long res_smem_bytes(const std::vector<Task>& tasks, int zs, int ds) {
   long long mx = 0;
-  for (const Task& k : tasks) {
-    const long long spr = (k.bx + 3) / 4;
-    const long long ps = (k.by + 2) * (4 * spr + 4) + 4;
-    mx = std::max(mx, (zs + 4) * ps + (ds ? zs * 4 * spr * k.by : 0));
-  }
+  for (const Task& k : tasks) mx = std::max(mx, res_smem_floats(k.bx, k.by, zs, ds != 0));
   return mx * 4;
 }
 
@@ -40,11 +37,12 @@ static bool res_fits(const std::vector<Task>& tasks, int nt, int kc, int zs, int
 }
 
 static void list_resident(Tuner& t, int mode, const std::vector<Task>& tasks, long long maxpts, int req_cluster,
-                          int req_threads, int req_slots, std::vector<LaunchShape>* out) {
+                          int req_threads, int req_slots, int req_variant, std::vector<LaunchShape>* out) {
   const int ntasks = (int)tasks.size();
   for (int v = 0; v < res_variant_count(); ++v) {
-    int nt, kc, zs, ds;
-    res_variant_info(v, &nt, &kc, &zs, &ds);
+    if (req_variant >= 0 && v != req_variant) continue;
+    int nt, kc, zs, ds, qr;
+    res_variant_info(v, &nt, &kc, &zs, &ds, &qr);
     if (req_threads && req_threads != nt) continue;
     const long long smem = res_smem_bytes(tasks, zs, ds);
     if (smem > 220 * 1024) continue;
@@ -72,7 +70,7 @@ static void list_resident(Tuner& t, int mode, const std::vector<Task>& tasks, lo
       r.smem = (size_t)smem;
       // rounds of the task queue x points each CTA handles per round
       const double rounds = std::ceil((double)ntasks / r.slots);
-      r.est = rounds * ((double)maxpts / c) * (1.0 + 0.02 * c);
+      r.est = rounds * ((double)maxpts / c) * (1.0 + 0.02 * c) * (qr ? 0.85 : 1.0);  // QR: one stencil per iteration
       out->push_back(r);
     }
   }
@@ -120,10 +118,10 @@ std::vector<long long> signature(int prec, int mode, int engine, const std::vect
 }
 
 int list_shapes(Tuner& t, int prec, int mode, int engine, const std::vector<Task>& tasks, long long maxpts,
-                int req_cluster, int req_threads, int req_slots, std::vector<LaunchShape>* out) {
+                int req_cluster, int req_threads, int req_slots, int req_variant, std::vector<LaunchShape>* out) {
   out->clear();
   if (prec == 1 && engine != 1) {
-    list_resident(t, mode, tasks, maxpts, req_cluster, req_threads, req_slots, out);
+    list_resident(t, mode, tasks, maxpts, req_cluster, req_threads, req_slots, req_variant, out);
     std::stable_sort(out->begin(), out->end(),
                      [](const LaunchShape& a, const LaunchShape& b) { return a.est < b.est; });
     if (engine == 2) return out->empty() ? (int)cudaErrorInvalidConfiguration : 0;
@@ -166,9 +164,10 @@ int list_shapes(Tuner& t, int prec, int mode, int engine, const std::vector<Task
 }
 
 int choose_shape(Tuner& t, int prec, int mode, int engine, const std::vector<Task>& tasks, long long maxpts,
-                 int req_cluster, int req_threads, int req_slots, LaunchShape* out) {
+                 int req_cluster, int req_threads, int req_slots, int req_variant, LaunchShape* out) {
   std::vector<LaunchShape> all;
-  const int rc = list_shapes(t, prec, mode, engine, tasks, maxpts, req_cluster, req_threads, req_slots, &all);
+  const int rc = list_shapes(t, prec, mode, engine, tasks, maxpts, req_cluster, req_threads, req_slots, req_variant,
+                             &all);
   if (rc) return rc;
   *out = all.front();
   return 0;

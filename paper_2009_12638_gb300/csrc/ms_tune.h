@@ -26,9 +26,16 @@ struct Tuner {
   std::map<std::tuple<int, int, int, int>, int> occ;
   // measured best shape per problem signature (see signature())
   std::map<std::vector<long long>, LaunchShape> best;
+  // sync mode, resident engine: measured ms per sweep of the persistent
+  // dataflow launch and of the per-sweep graph, per signature + shape (< 0: not yet)
+  struct ModeMs {
+    double flow = -1.0, sweep = -1.0;
+  };
+  std::map<std::vector<long long>, ModeMs> mode_ms;
   void release() {
     occ.clear();
     best.clear();
+    mode_ms.clear();
   }
 };
 
@@ -39,11 +46,12 @@ std::vector<long long> signature(int prec, int mode, int engine, const std::vect
 // Every launchable shape for the problem, best model estimate first (the
 // resident engine's shapes, when it applies, precede the streaming ones).
 // Explicit non-zero requests restrict the list.  Returns a cudaError_t value.
+// req_variant >= 0 keeps only that row of the resident variant table.
 int list_shapes(Tuner& t, int prec, int mode, int engine, const std::vector<Task>& tasks, long long maxpts,
-                int req_cluster, int req_threads, int req_slots, std::vector<LaunchShape>* out);
+                int req_cluster, int req_threads, int req_slots, int req_variant, std::vector<LaunchShape>* out);
 
 // The first shape of list_shapes.
 int choose_shape(Tuner& t, int prec, int mode, int engine, const std::vector<Task>& tasks, long long maxpts,
-                 int req_cluster, int req_threads, int req_slots, LaunchShape* out);
+                 int req_cluster, int req_threads, int req_slots, int req_variant, LaunchShape* out);
 
 }  // namespace ms

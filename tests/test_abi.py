@@ -47,10 +47,10 @@ def test_ctypes_structs_match_c_layout(tmp_path):
 #include <stddef.h>
 #include "ms.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu\n", sizeof(ms_opts), offsetof(ms_opts, outer_tol), offsetof(ms_opts, res_hist),
-         offsetof(ms_opts, slow_ns), offsetof(ms_opts, time_limit_ms));
-  printf("%zu %zu %zu %zu\n", sizeof(ms_stats), offsetof(ms_stats, lups), offsetof(ms_stats, per_rhs_rel),
-         offsetof(ms_stats, slots));
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(ms_opts), offsetof(ms_opts, outer_tol), offsetof(ms_opts, res_hist),
+         offsetof(ms_opts, slow_ns), offsetof(ms_opts, time_limit_ms), offsetof(ms_opts, variant));
+  printf("%zu %zu %zu %zu %zu\n", sizeof(ms_stats), offsetof(ms_stats, lups), offsetof(ms_stats, per_rhs_rel),
+         offsetof(ms_stats, slots), offsetof(ms_stats, variant));
   return 0;
 }
 ''')
@@ -59,8 +59,9 @@ int main(void) {
     a, b = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:2]
     O, S = _lib.Opts, _lib.Stats
     assert [int(v) for v in a.split()] == [ctypes.sizeof(O), O.outer_tol.offset, O.res_hist.offset,
-                                          O.slow_ns.offset, O.time_limit_ms.offset]
-    assert [int(v) for v in b.split()] == [ctypes.sizeof(S), S.lups.offset, S.per_rhs_rel.offset, S.slots.offset]
+                                          O.slow_ns.offset, O.time_limit_ms.offset, O.variant.offset]
+    assert [int(v) for v in b.split()] == [ctypes.sizeof(S), S.lups.offset, S.per_rhs_rel.offset, S.slots.offset,
+                                          S.variant.offset]
 
 
 def test_default_opts(lib):
@@ -68,6 +69,27 @@ def test_default_opts(lib):
     lib.ms_default_opts(ctypes.byref(o))
     assert (o.mode, o.precision, o.inner_rtol, o.inner_maxit, o.outer_tol) == (0, 1, 1e-6, 50, 1e-8)
     assert o.slow_block == -1 and o.use_graph == 1
+    assert o.variant == -1
+
+
+def test_resident_variant_table(lib):
+    from paper_2009_12638_gb300 import resident_variants
+    rows = resident_variants()
+    assert len(rows) >= 2
+    for r in rows:
+        assert r["threads"] in (256, 512, 1024) and r["strips"] >= 1 and r["planes"] >= 1
+        assert r["d_smem"] in (0, 1) and r["q_regs"] in (0, 1)
+    # every layout that keeps q in registers has a twin that does not (the
+    # GPU tests compare the two bit for bit)
+    key = lambda r: (r["threads"], r["strips"], r["planes"], r["d_smem"])  # noqa: E731
+    plain = {key(r) for r in rows if not r["q_regs"]}
+    assert all(key(r) in plain for r in rows if r["q_regs"])
+    n = ctypes.c_int(0)
+    t = ctypes.c_int(0)
+    assert lib.ms_resident_variant(len(rows), ctypes.byref(n), ctypes.byref(t), None, None, None, None) == \
+        _lib.MS_ERR_ARG
+    assert n.value == len(rows)
+    assert lib.ms_resident_variant(-1, None, None, None, None, None, None) == _lib.MS_ERR_ARG
 
 
 def test_boundary_size(lib):
@@ -119,11 +141,18 @@ def test_solve_rejects_bad_arguments_before_device_work(lib):
         assert lib.ms_solve(h, None, None, None, ctypes.byref(o), None, None) == _lib.MS_ERR_ARG
         dummy = ctypes.c_void_p(16)  # never dereferenced: options are checked first
         for field, value in [("mode", 7), ("precision", 3), ("inner_maxit", -1), ("threads", 100),
-                             ("cluster", 17), ("outer_tol", -1.0), ("time_limit_ms", -5.0)]:
+                             ("cluster", 17), ("outer_tol", -1.0), ("time_limit_ms", -5.0), ("variant", -2),
+                             ("variant", 10000)]:
             o2 = _lib.Opts()
             lib.ms_default_opts(ctypes.byref(o2))
             setattr(o2, field, value)
             assert lib.ms_solve(h, None, None, dummy, ctypes.byref(o2), None, None) == _lib.MS_ERR_ARG, field
+        # a resident layout with FP64 or the streaming engine is rejected before device work
+        for prec, eng in [(0, 0), (1, 1)]:
+            o2 = _lib.Opts()
+            lib.ms_default_opts(ctypes.byref(o2))
+            o2.variant, o2.precision, o2.engine = 0, prec, eng
+            assert lib.ms_solve(h, None, None, dummy, ctypes.byref(o2), None, None) == _lib.MS_ERR_ARG
         assert lib.ms_residual(h, None, None, None, None, None) == _lib.MS_ERR_ARG
         assert lib.ms_face_gather(h, None, None, None) == _lib.MS_ERR_ARG
     finally:

@@ -14,7 +14,7 @@ import pytest
 import torch
 
 import oracle
-from paper_2009_12638_gb300 import Grid, inputs
+from paper_2009_12638_gb300 import Grid, MsError, inputs
 
 pytestmark = pytest.mark.gpu
 
@@ -360,6 +360,40 @@ def test_resident_persistent_and_per_sweep_agree(persistent):
     np.testing.assert_array_equal(x1.cpu().numpy(), x2.cpu().numpy())
     xc, sc = g.solve(bnd=b, precision="mixed", engine="resident", persistent=persistent, history=True)
     assert sc.status == 0 and sc.rel_residual < 1e-8
+
+
+@pytest.mark.parametrize("case", RES_CASES[:2] + RES_CASES[3:])
+def test_resident_q_in_registers_is_bit_identical(case):
+    """Keeping q = A p in registers (one stencil per CG iteration) and moving
+    d += alpha p to the next pass performs the same FMAs in the same order as
+    recomputing the stencil: every layout and its q-in-registers twin give
+    the same iterates bit for bit, sweep after sweep."""
+    from paper_2009_12638_gb300 import resident_variants
+    nx, ny, nz, cx, cy, cz = case
+    bnd = np.random.default_rng(54).uniform(-1, 1, size=(2, inputs.boundary_size(nx, ny, nz)))
+    g = make_grid(nx, ny, nz, 2, cx, cy, cz)
+    rows = resident_variants()
+    key = lambda r: (r["threads"], r["strips"], r["planes"], r["d_smem"])  # noqa: E731
+    plain = {key(r): v for v, r in enumerate(rows) if not r["q_regs"]}
+    compared = 0
+    for w, r in enumerate(rows):
+        if not r["q_regs"]:
+            continue
+        v = plain[key(r)]
+        res = []
+        for var in (v, w):
+            try:
+                x, st = g.solve(bnd=cuda(bnd), precision="mixed", variant=var, persistent=False, outer_tol=0.0,
+                                outer_maxit=4)
+            except MsError:
+                break  # this layout does not fit the blocks
+            assert st.variant == var and st.outer_its == 4
+            res.append((x.cpu().numpy(), st.inner_its))
+        if len(res) == 2:
+            np.testing.assert_array_equal(res[0][0], res[1][0])
+            assert res[0][1] == res[1][1]
+            compared += 1
+    assert compared >= 2
 
 
 def test_resident_uneven_multi_rhs():
