@@ -228,11 +228,13 @@ def main():
         return grid.solve(bnd=bnd, out=x, **dict(opts, **extra))
 
     if args.sweeps:
-        # a short, fixed run for ncu captures: the shape the autotuner would pick, plain launches
-        _, st = solve_once(outer_tol=0.0, outer_maxit=args.sweeps, use_graph=False)
+        # a short, fixed run for ncu captures: the shape the autotuner would pick, one plain
+        # launch of the sweep kernel per sweep (the launch mode of the timed solves)
+        _, st = solve_once(outer_tol=0.0, outer_maxit=args.sweeps, use_graph=False, persistent=False)
         torch.cuda.synchronize(dev)
         print(json.dumps({"sweeps": args.sweeps, "status": st.status_name, "engine": st.engine,
-                          "shape": [st.cluster, st.threads, st.slots], "time_ms": st.time_ms}))
+                          "variant": st.variant, "shape": [st.cluster, st.threads, st.slots],
+                          "time_ms": st.time_ms}))
         return
 
     for _ in range(max(args.warmup, 3)):
