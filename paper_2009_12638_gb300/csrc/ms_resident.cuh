@@ -71,32 +71,33 @@ __device__ __forceinline__ void st_cluster_f32(float* local, unsigned rank, floa
   asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(cl_map(local, rank)), "f"(v) : "memory");
 }
 
-// Cluster-wide FP32 sum.  Each warp stores its total into slot[rank][warp] of
-// every CTA; after the single cluster barrier EVERY warp of every CTA adds
-// all slots in the same order, so every thread holds the bit-identical total
-// and no CTA-wide barrier or broadcast is needed.  `slots` must not be
-// reused by another reduction before the next cluster barrier.
+// Cluster-wide FP32 sum.  Warp totals (xor butterfly: every lane holds the
+// same bits) go to `wsum`; after one CTA barrier warp 0 adds them and stores
+// the CTA total into slot[rank] of every CTA; after the cluster barrier
+// EVERY warp adds the csize slots in the same order, so every thread of the
+// cluster holds the bit-identical total.  Pre-reducing inside the CTA keeps
+// the remote stores per sum at csize per CTA (instead of one per warp and
+// CTA), which shortens the cluster barrier's release.  `slots` and `wsum`
+// must not be reused by another sum before the next cluster barrier.
 template <int NT>
-__device__ __forceinline__ float cluster_sum_f32(float v, float* slots, unsigned rank, unsigned csize) {
+__device__ __forceinline__ float cluster_sum_f32(float v, float* slots, float* wsum, unsigned rank, unsigned csize) {
   constexpr int NW = NT / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  v = __shfl_sync(0xffffffffu, v, 0);
-  if (lane < (int)csize) st_cluster_f32(&slots[rank * NW + warp], (unsigned)lane, v);
-  cl_barrier();
-  // csize * NW slots, NW a multiple of 4: float4 loads, lane l takes float4s l, l + 32, ...
-  static_assert(NW % 4 == 0, "slots are summed as float4");
-  const float4* s4 = reinterpret_cast<const float4*>(slots);
-  const int n4 = (int)csize * (NW / 4);
-  float acc = 0.f;
-  for (int i = lane; i < n4; i += 32) {
-    const float4 w = s4[i];
-    acc += (w.x + w.y) + (w.z + w.w);
-  }
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) wsum[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    float t = lane < NW ? wsum[lane] : 0.f;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  return __shfl_sync(0xffffffffu, acc, 0);
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane < (int)csize) st_cluster_f32(&slots[rank], (unsigned)lane, t);
+  }
+  cl_barrier();
+  float acc = lane < (int)csize ? slots[lane] : 0.f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  return acc;
 }
 
 // 7-point stencil q = 6p - sum(nbrs) on the 4 points of a strip.  y and z
@@ -155,10 +156,11 @@ __device__ __forceinline__ Strips<KC> make_strips(const ResGeo& g) {
   return s;
 }
 
-// Reduction slots of the resident engine (FP32, one per warp per CTA).
+// Reduction slots of the resident engine (FP32): CTA totals, one per rank,
+// and this CTA's warp totals, for the two sums of a CG iteration.
 struct ResRed {
-  __align__(16) float eta[kMaxCluster * 32];
-  __align__(16) float gam[kMaxCluster * 32];
+  float eta[kMaxCluster], gam[kMaxCluster];
+  float weta[32], wgam[32];
 };
 
 // Inner CG on the resident state.  On entry r4 holds r (padding lanes 0),
@@ -258,7 +260,7 @@ __device__ int resident_cg(float4 (&r4)[KC][ZS], float4 (&d4)[DS ? 1 : KC][DS ? 
         c = zp;
       }
     }
-    const float eta = cluster_sum_f32<NT>(eta_loc, rr.eta, rank, csize);
+    const float eta = cluster_sum_f32<NT>(eta_loc, rr.eta, rr.weta, rank, csize);
     if (!(eta > 0.f)) break;  // curvature breakdown or NaN: keep d from earlier steps
     alpha = gamma / eta;
     // ---------------- pass B: (QR = false: d += alpha p,) r -= alpha q, gamma = r.r, push boundary r
@@ -296,7 +298,7 @@ __device__ int resident_cg(float4 (&r4)[KC][ZS], float4 (&d4)[DS ? 1 : KC][DS ? 
       }
     }
     pending = QR;
-    const float gnew = cluster_sum_f32<NT>(g_loc, rr.gam, rank, csize);
+    const float gnew = cluster_sum_f32<NT>(g_loc, rr.gam, rr.wgam, rank, csize);
     m += 1;
     if (sqrtf(gnew) <= stop || m >= inner_maxit) break;
     beta = gnew / gamma;
