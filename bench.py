@@ -339,6 +339,18 @@ def main():
             ms = e0.elapsed_time(e1)
             comp[name] = {"status": sc.status_name, "time_to_tol_s": ms / 1e3, "outer_its": sc.outer_its,
                           "rel_residual": sc.rel_residual, "glups": sc.lups / (ms * 1e-3) / 1e9}
+        # one global FP64 CG on the whole grid (no blocks), same stop rule and tolerance
+        x.zero_()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, sc = grid.gcg_solve(bnd=bnd, out=x, outer_tol=opts["outer_tol"], time_limit_ms=120000)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        comp["global_fp64_cg"] = {"status": sc.status_name, "time_to_tol_s": ms / 1e3, "iterations": sc.outer_its,
+                                  "rel_residual": sc.rel_residual, "glups": sc.lups / (ms * 1e-3) / 1e9}
         out["compare"] = comp
         if "fp64_sync" in comp and comp["fp64_sync"]["status"] == "OK":
             out["speedup_vs_fp64_sync"] = comp["fp64_sync"]["time_to_tol_s"] / out["time_to_tol_s"]

@@ -215,6 +215,26 @@ MS_API int ms_residual_noalloc(ms_grid* grid, const double* f, const double* bnd
  * rows.  Host only, no device work. */
 MS_API int ms_resident_variant(int v, int* count, int* threads, int* strips, int* planes, int* d_smem, int* q_regs);
 
+/* One global conjugate-gradient solve of A x = f + lift(bnd) on the whole
+ * grid, in FP64, with no block splitting: the single-matrix Krylov method the
+ * multisplitting solve is compared against on the same GPU.  CG is the inner
+ * method of sections 2.2 and 3 applied to A itself; the stop rule is the one
+ * of section 2.1, ||r_k|| < outer_tol ||bhat|| (strict, absolute if
+ * ||bhat|| = 0), on the CG recurrence residual, tested before iteration k
+ * (k = 0 included).  Arguments as for ms_solve (device pointers, x = x0 in,
+ * solution out, stream = cudaStream_t or NULL); of opts only outer_tol,
+ * outer_maxit (iteration cap) and time_limit_ms (device-side budget, applied
+ * from the next iteration) are used, every other field is ignored and the
+ * arithmetic is FP64 throughout.  Workspace: three vectors of nrhs x npts
+ * doubles, kept by the grid handle.  stats: outer_its = iterations (max over
+ * rhs), inner_its = iterations summed over rhs, lups = iterations x points +
+ * the three residual evaluations, rel_residual = the true final relative
+ * residual (max over rhs), engine = 0, variant = -1.  Returns MS_OK, or
+ * MS_ERR_NOT_CONVERGED / MS_ERR_TIMEOUT (x holds the last iterate), or
+ * MS_ERR_ARG / MS_ERR_CUDA / MS_ERR_OOM. */
+MS_API int ms_gcg_solve(ms_grid* grid, const double* f, const double* bnd, double* x, const ms_opts* opts,
+                        ms_stats* stats, void* stream);
+
 MS_API int ms_destroy(ms_grid* grid);
 
 /* Message for the last failure on this handle (or of ms_create_grid when

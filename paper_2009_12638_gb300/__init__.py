@@ -196,6 +196,16 @@ class Grid:
         engine ('auto'|'streaming'|'resident'), persistent, variant (resident
         layout row, see resident_variants(); -1 = tuned).
         """
+        return self._call(self._lib.ms_solve, f, bnd, x0, out, history, opts)
+
+    def gcg_solve(self, f=None, bnd=None, x0=None, out=None, **opts):
+        """ms_gcg_solve: one global FP64 CG solve of A x = f + lift(bnd) on the
+        whole grid (no blocks), the comparison method; returns (x, SolveStats).
+        Uses opts outer_tol, outer_maxit (iteration cap) and time_limit_ms;
+        stats.outer_its is the iteration count."""
+        return self._call(self._lib.ms_gcg_solve, f, bnd, x0, out, False, opts)
+
+    def _call(self, fn, f, bnd, x0, out, history, opts):
         f = self._field(f, "f", self.shape)
         bnd = self._field(bnd, "bnd", (self.nrhs, self.nbnd))
         if out is None:
@@ -218,8 +228,8 @@ class Grid:
         st.per_rhs_outer_its = per_its
         st.per_rhs_rel = per_rel
         with torch.cuda.device(self.device):
-            rc = self._lib.ms_solve(self._h, _ptr(f), _ptr(bnd), _ptr(out), ctypes.byref(o), ctypes.byref(st),
-                                    _stream_handle(self.device))
+            rc = fn(self._h, _ptr(f), _ptr(bnd), _ptr(out), ctypes.byref(o), ctypes.byref(st),
+                    _stream_handle(self.device))
         if rc not in (_lib.MS_OK, _lib.MS_ERR_NOT_CONVERGED, _lib.MS_ERR_TIMEOUT):
             self._check(rc)
         stats = SolveStats(rc, st.outer_its, st.inner_its, st.lups, st.rel_residual, st.time_ms, st.launches,

@@ -26,7 +26,7 @@ PRECISION = {"fp64": 0, "mixed": 1}
 # Symbols declared in include/ms.h (checked by the CPU tests).
 EXPORTS = ("ms_boundary_size", "ms_default_opts", "ms_create_grid", "ms_partition", "ms_get_cuts", "ms_solve",
            "ms_solve_host", "ms_residual", "ms_face_gather", "ms_destroy", "ms_last_error",
-           "ms_residual_noalloc", "ms_resident_variant")
+           "ms_residual_noalloc", "ms_resident_variant", "ms_gcg_solve")
 NOALLOC_MAX_RHS = 1024
 
 
@@ -99,6 +99,7 @@ def load(path: str = LIB_PATH):
         lib.ms_get_cuts.argtypes = [vp, ip, ip, ip]
         lib.ms_solve.argtypes = [vp, vp, vp, vp, ctypes.POINTER(Opts), ctypes.POINTER(Stats), vp]
         lib.ms_solve_host.argtypes = [vp, vp, vp, vp, ctypes.POINTER(Opts), ctypes.POINTER(Stats), vp]
+        lib.ms_gcg_solve.argtypes = [vp, vp, vp, vp, ctypes.POINTER(Opts), ctypes.POINTER(Stats), vp]
         lib.ms_residual.argtypes = [vp, vp, vp, vp, dp, vp]
         lib.ms_face_gather.argtypes = [vp, vp, vp, vp]
         lib.ms_residual_noalloc.argtypes = [vp, vp, vp, vp, vp, vp]

@@ -85,6 +85,7 @@ struct ms_grid {
   DevBuf host_io;  // device copies for ms_solve_host: f, bnd, x
   DevBuf async_ws; // face buffers, halos, seq counters (async mode)
   DevBuf flow_ws;  // tickets, per-task progress, per-sweep counters (persistent sync mode)
+  DevBuf gcg_ws;   // global CG: r, p, q, partial sums, control words
   Tuner tuner;
   long long npts() const { return (long long)nx * ny * nz; }
   long long nbnd() const { return ms_boundary_size(nx, ny, nz); }
@@ -371,6 +372,161 @@ extern "C" int ms_face_gather(ms_grid* g, const double* lam, double* grad_bnd, v
   return MS_OK;
 }
 
+extern "C" int ms_gcg_solve(ms_grid* g, const double* f, const double* bnd, double* x, const ms_opts* opts,
+                            ms_stats* st, void* stream) {
+  if (!g) return MS_ERR_ARG;
+  if (!x) return fail(g, MS_ERR_ARG, "ms_gcg_solve: x is NULL");
+  ms_opts o;
+  if (opts) o = *opts;
+  else ms_default_opts(&o);
+  if (!(o.outer_tol >= 0.0) || o.outer_maxit < 0 || !(o.time_limit_ms >= 0.0))
+    return fail(g, MS_ERR_ARG, "ms_gcg_solve: outer_tol, outer_maxit and time_limit_ms must be >= 0");
+  cudaGetLastError();  // a stale non-sticky error from unrelated work must not fail this solve
+  cudaStream_t s = (cudaStream_t)stream;
+  const Geo G = g->geo();
+  const int nb = gcg_blocks(G);
+  const size_t vec = (size_t)G.nrhs * G.npts * sizeof(double);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t r = off;
+    off += (bytes + 255) / 256 * 256;
+    return r;
+  };
+  const size_t o_r = take(vec), o_p = take(vec), o_q = take(vec);
+  const size_t o_ctl = off;  // everything after this is zeroed per solve
+  const size_t o_rr = take(2 * (size_t)G.nrhs * nb * sizeof(double)), o_pq = take((size_t)G.nrhs * nb * sizeof(double));
+  const size_t o_norm = take(2 * (size_t)G.nrhs * sizeof(double)), o_state = take((size_t)G.nrhs * sizeof(int));
+  const size_t o_kf = take((size_t)G.nrhs * sizeof(int)), o_k = take(sizeof(int)), o_stop = take(sizeof(int));
+  const size_t o_t = take(sizeof(unsigned long long));
+  MS_CUDA(g, g->gcg_ws.reserve(off));
+  char* w = g->gcg_ws.as<char>();
+  MS_CUDA(g, cudaMemsetAsync(w + o_ctl, 0, off - o_ctl, s));  // state = kActive, counters 0
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  struct Ev {
+    cudaEvent_t* a;
+    cudaEvent_t* b;
+    ~Ev() {
+      if (*a) cudaEventDestroy(*a);
+      if (*b) cudaEventDestroy(*b);
+    }
+  } evg{&ev0, &ev1};
+  MS_CUDA(g, cudaEventCreate(&ev0));
+  MS_CUDA(g, cudaEventCreate(&ev1));
+  MS_CUDA(g, cudaEventRecord(ev0, s));
+  double* norms = reinterpret_cast<double*>(w + o_norm);
+  int rc = run_resid(g, f, bnd, x, norms, nullptr, s);  // norms[2s+1] = ||bhat||^2
+  if (rc != MS_OK) return rc;
+  GcgArgs a;
+  a.g = G;
+  a.f = f;
+  a.bnd = bnd;
+  a.x = x;
+  a.r = reinterpret_cast<double*>(w + o_r);
+  a.p = reinterpret_cast<double*>(w + o_p);
+  a.q = reinterpret_cast<double*>(w + o_q);
+  a.part_rr = reinterpret_cast<double*>(w + o_rr);
+  a.part_pq = reinterpret_cast<double*>(w + o_pq);
+  a.nb = nb;
+  a.norms = norms;
+  a.tol = o.outer_tol;
+  a.maxit = o.outer_maxit;
+  a.state = reinterpret_cast<int*>(w + o_state);
+  a.k_final = reinterpret_cast<int*>(w + o_kf);
+  a.k_dev = reinterpret_cast<int*>(w + o_k);
+  a.stop_all = reinterpret_cast<int*>(w + o_stop);
+  a.t_start = reinterpret_cast<unsigned long long*>(w + o_t);
+  a.budget_ns = o.time_limit_ms > 0.0 ? (long long)(o.time_limit_ms * 1.0e6) : 0;
+  a.use_cond = 0;
+  a.cond = 0;
+  MS_CUDA(g, launch_gcg_init(a, s));
+  // the iterations: ONE graph launch, a conditional WHILE node over [p, q, x kernels]
+  {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t ce = cudaGraphCreate(&graph, 0);
+    cudaGraphConditionalHandle cond = 0;
+    if (ce == cudaSuccess) ce = cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (ce == cudaSuccess) ce = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+    if (ce == cudaSuccess) {
+      cudaGraph_t body = cp.conditional.phGraph_out[0];
+      cudaStream_t cs = nullptr;
+      ce = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+      if (ce == cudaSuccess) {
+        GcgArgs ab = a;
+        ab.use_cond = 1;
+        ab.cond = cond;
+        ce = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        const cudaError_t c1 = ce == cudaSuccess ? launch_gcg_iteration(ab, cs) : ce;
+        const cudaError_t c2 = ce == cudaSuccess ? cudaStreamEndCapture(cs, &body) : cudaSuccess;
+        if (ce == cudaSuccess) ce = c1 != cudaSuccess ? c1 : c2;
+        cudaStreamDestroy(cs);
+      }
+    }
+    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
+    if (ce == cudaSuccess) ce = cudaGraphLaunch(exec, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    MS_CUDA(g, ce);
+  }
+  // true residual of the returned x
+  rc = run_resid(g, f, bnd, x, norms, nullptr, s);
+  if (rc != MS_OK) return rc;
+  MS_CUDA(g, cudaEventRecord(ev1, s));
+  std::vector<int> h_state(G.nrhs), h_kf(G.nrhs);
+  std::vector<double> h_norm(2 * (size_t)G.nrhs);
+  int h_k = 0;
+  MS_CUDA(g, cudaMemcpyAsync(h_state.data(), a.state, G.nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
+  MS_CUDA(g, cudaMemcpyAsync(h_kf.data(), a.k_final, G.nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
+  MS_CUDA(g, cudaMemcpyAsync(h_norm.data(), norms, h_norm.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  MS_CUDA(g, cudaMemcpyAsync(&h_k, a.k_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MS_CUDA(g, cudaStreamSynchronize(s));
+  float ms_el = 0.f;
+  MS_CUDA(g, cudaEventElapsedTime(&ms_el, ev0, ev1));
+  int status = MS_OK;
+  long long its_total = 0;
+  int its_max = 0;
+  double relmax = 0.0;
+  for (int r = 0; r < G.nrhs; ++r) {
+    if (h_state[r] == kStopped) status = MS_ERR_NOT_CONVERGED;  // iteration cap or time budget
+    its_total += h_kf[r];
+    its_max = std::max(its_max, h_kf[r]);
+    const double rel = h_norm[2 * r + 1] > 0.0 ? std::sqrt(h_norm[2 * r]) / std::sqrt(h_norm[2 * r + 1])
+                                               : std::sqrt(h_norm[2 * r]);
+    relmax = std::max(relmax, rel);
+    if (st && st->per_rhs_outer_its) st->per_rhs_outer_its[r] = h_kf[r];
+    if (st && st->per_rhs_rel) st->per_rhs_rel[r] = rel;
+  }
+  if (status == MS_ERR_NOT_CONVERGED && a.budget_ns > 0) {
+    int h_stop = 0;
+    MS_CUDA(g, cudaMemcpy(&h_stop, a.stop_all, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h_stop) status = MS_ERR_TIMEOUT;
+  }
+  if (st) {
+    st->status = status;
+    st->outer_its = its_max;
+    st->inner_its = its_total;
+    st->lups = its_total * G.npts + 3LL * G.nrhs * G.npts;  // iterations + initial residual + two true residuals
+    st->rel_residual = relmax;
+    st->time_ms = ms_el;
+    st->launches = 3 + 3 * (h_k + 1) + 2;
+    st->cluster = 1;
+    st->threads = 256;
+    st->slots = nb;
+    st->sweep_ms = 0.0;
+    st->sweep_launches = 0;
+    st->engine = 0;
+    st->variant = -1;
+  }
+  return status;
+}
+
 extern "C" int ms_resident_variant(int v, int* count, int* threads, int* strips, int* planes, int* d_smem,
                                    int* q_regs) {
   const int n = ms::res_variant_count();
@@ -399,6 +555,7 @@ extern "C" int ms_destroy(ms_grid* g) {
   g->host_io.release();
   g->async_ws.release();
   g->flow_ws.release();
+  g->gcg_ws.release();
   g->tuner.release();
   delete g;
   return MS_OK;

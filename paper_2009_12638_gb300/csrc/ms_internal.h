@@ -142,6 +142,34 @@ struct ResidArgs {
   int nblk;
 };
 
+// One global FP64 CG solve on the whole grid (ms_gcg.cu).
+struct GcgArgs {
+  Geo g;
+  const double* f;    // [nrhs][npts] or null
+  const double* bnd;  // [nrhs][nbnd] or null
+  double* x;          // in: x0, out: solution
+  double* r;          // [nrhs][npts] workspace
+  double* p;
+  double* q;
+  double* part_rr;  // [2][nrhs][nb]: r.r partials, by iteration parity
+  double* part_pq;  // [nrhs][nb]
+  int nb;           // CTAs per rhs
+  const double* norms;  // [nrhs][2]; norms[2s+1] = ||bhat||^2
+  double tol;
+  int maxit;
+  int* state;    // [nrhs] kActive / kConverged / kStopped
+  int* k_final;  // [nrhs] iterations done when the rhs stopped
+  int* k_dev;    // iteration counter
+  int* stop_all;
+  unsigned long long* t_start;
+  long long budget_ns;  // 0 = no time budget
+  int use_cond;
+  cudaGraphConditionalHandle cond;
+};
+int gcg_blocks(const Geo& g);
+cudaError_t launch_gcg_init(const GcgArgs& a, cudaStream_t s);
+cudaError_t launch_gcg_iteration(const GcgArgs& a, cudaStream_t s);
+
 // handle accessors for entry points defined outside ms_api.cu
 Geo grid_geo(const ms_grid* g);
 int grid_fail(ms_grid* g, int code, const char* fmt, ...);

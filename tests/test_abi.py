@@ -154,6 +154,13 @@ def test_solve_rejects_bad_arguments_before_device_work(lib):
             o2.variant, o2.precision, o2.engine = 0, prec, eng
             assert lib.ms_solve(h, None, None, dummy, ctypes.byref(o2), None, None) == _lib.MS_ERR_ARG
         assert lib.ms_residual(h, None, None, None, None, None) == _lib.MS_ERR_ARG
+        # global CG: NULL x and negative tolerances or caps are rejected before device work
+        assert lib.ms_gcg_solve(h, None, None, None, ctypes.byref(o), None, None) == _lib.MS_ERR_ARG
+        for field, value in [("outer_tol", -1.0), ("outer_maxit", -1), ("time_limit_ms", -1.0)]:
+            o2 = _lib.Opts()
+            lib.ms_default_opts(ctypes.byref(o2))
+            setattr(o2, field, value)
+            assert lib.ms_gcg_solve(h, None, None, dummy, ctypes.byref(o2), None, None) == _lib.MS_ERR_ARG, field
         assert lib.ms_face_gather(h, None, None, None) == _lib.MS_ERR_ARG
     finally:
         lib.ms_destroy(h)
