@@ -325,8 +325,9 @@ def main():
     if rank == 0 and not args.no_compare:
         comp = {}
         for name, extra in [("fp64_sync", dict(precision="fp64", mode="sync")),
-                            ("mixed_async", dict(precision="mixed", mode="async"))]:
-            if extra["precision"] == args.precision and extra["mode"] == args.mode:
+                            ("mixed_async", dict(precision="mixed", mode="async")),
+                            ("mixed_sync_adaptive_inner", dict(precision="mixed", mode="sync", inner_adapt=True))]:
+            if extra["precision"] == args.precision and extra["mode"] == args.mode and "inner_adapt" not in extra:
                 continue
             x.zero_()
             torch.cuda.synchronize(dev)
@@ -339,6 +340,8 @@ def main():
             ms = e0.elapsed_time(e1)
             comp[name] = {"status": sc.status_name, "time_to_tol_s": ms / 1e3, "outer_its": sc.outer_its,
                           "rel_residual": sc.rel_residual, "glups": sc.lups / (ms * 1e-3) / 1e9}
+            if "inner_adapt" in extra:
+                comp[name]["inner_rtol_final"] = sc.inner_rtol_final
         # one global FP64 CG on the whole grid (no blocks), same stop rule and tolerance
         x.zero_()
         torch.cuda.synchronize(dev)

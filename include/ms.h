@@ -98,6 +98,14 @@ typedef struct {
                             registers and shared memory of the cluster; MIXED + SYNC, blocks that fit) */
   int variant;           /* resident engine: -1 (default) = chosen by the autotuner; v >= 0 = row v of
                             the variant table (ms_resident_variant), for tests and profiling */
+  int inner_adapt;       /* sync mode: 1 = choose the inner tolerance at run time (default 0 = use
+                            inner_rtol).  Runtime adaptation of the inner solve, the paper's closing
+                            suggestion (sections 3.2 and 5): after every sweep a per-rhs controller
+                            charges the sweep's decrease of log(residual) to the relative inner
+                            tolerance it ran with, against its work (inner lattice updates plus the
+                            residual and update), tries the neighbouring tolerances of a ladder
+                            (0.8 ... 1e-3) in rounds of 8 sweeps each and keeps the most efficient;
+                            inner_maxit still caps every inner solve.  Deterministic (no clocks). */
 } ms_opts;
 
 typedef struct {
@@ -116,6 +124,8 @@ typedef struct {
   int engine;                  /* inner-CG engine used: 1 streaming, 2 resident */
   int variant;                 /* launch variant used: >= 0 resident table row, -1 scalar streaming,
                                   -2 vectorised (float4) streaming */
+  double inner_rtol_final;     /* the inner tolerance of the last sweep (opts.inner_adapt: max over
+                                  rhs of the controller's choice; else opts.inner_rtol) */
 } ms_stats;
 
 /* Number of doubles in one rhs's packed boundary array. */

@@ -68,6 +68,7 @@ class SolveStats:
     sweep_launches: int = 0
     engine: int = 0
     variant: int = -1
+    inner_rtol_final: float = 0.0
     history: np.ndarray | None = None
 
     @property
@@ -85,7 +86,8 @@ def _stream_handle(device):
 
 def _make_opts(lib, mode="sync", precision="mixed", inner_rtol=1e-6, inner_maxit=50, outer_tol=1e-8,
                outer_maxit=100000, time_limit_ms=0.0, cluster=0, threads=0, slots=0, check_every=0, use_graph=True,
-               slow_block=-1, slow_ns=0, profile=False, engine="auto", persistent="auto", variant=-1):
+               slow_block=-1, slow_ns=0, profile=False, engine="auto", persistent="auto", variant=-1,
+               inner_adapt=False):
     o = _lib.Opts()
     lib.ms_default_opts(ctypes.byref(o))
     o.mode = _lib.MODE[mode] if isinstance(mode, str) else int(mode)
@@ -107,6 +109,7 @@ def _make_opts(lib, mode="sync", precision="mixed", inner_rtol=1e-6, inner_maxit
         persistent, bool) else int(persistent)
     o.engine = {"auto": 0, "streaming": 1, "resident": 2}[engine] if isinstance(engine, str) else int(engine)
     o.variant = int(variant)
+    o.inner_adapt = 1 if inner_adapt else 0
     return o
 
 
@@ -194,7 +197,8 @@ class Grid:
         inner_maxit, outer_tol, outer_maxit, time_limit_ms, cluster, threads,
         slots, check_every, use_graph, slow_block, slow_ns, profile,
         engine ('auto'|'streaming'|'resident'), persistent, variant (resident
-        layout row, see resident_variants(); -1 = tuned).
+        layout row, see resident_variants(); -1 = tuned), inner_adapt (sync:
+        choose the inner tolerance at run time).
         """
         return self._call(self._lib.ms_solve, f, bnd, x0, out, history, opts)
 
@@ -234,7 +238,7 @@ class Grid:
             self._check(rc)
         stats = SolveStats(rc, st.outer_its, st.inner_its, st.lups, st.rel_residual, st.time_ms, st.launches,
                            st.cluster, st.threads, st.slots, list(per_its), list(per_rel), st.sweep_ms,
-                           st.sweep_launches, st.engine, st.variant)
+                           st.sweep_launches, st.engine, st.variant, st.inner_rtol_final)
         if hist is not None:
             stats.history = hist
         return out, stats
@@ -264,7 +268,7 @@ class Grid:
             self._check(rc)
         return x, SolveStats(rc, st.outer_its, st.inner_its, st.lups, st.rel_residual, st.time_ms, st.launches,
                              st.cluster, st.threads, st.slots, [], [], st.sweep_ms, st.sweep_launches, st.engine,
-                             st.variant)
+                             st.variant, st.inner_rtol_final)
 
     def residual(self, x, f=None, bnd=None):
         """True relative residual per rhs (absolute where ||bhat|| = 0), computed on the GPU."""

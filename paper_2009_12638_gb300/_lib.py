@@ -51,6 +51,7 @@ class Opts(ctypes.Structure):
         ("persistent", ctypes.c_int),
         ("engine", ctypes.c_int),
         ("variant", ctypes.c_int),
+        ("inner_adapt", ctypes.c_int),
     ]
 
 
@@ -72,6 +73,7 @@ class Stats(ctypes.Structure):
         ("sweep_launches", ctypes.c_int),
         ("engine", ctypes.c_int),
         ("variant", ctypes.c_int),
+        ("inner_rtol_final", ctypes.c_double),
     ]
 
 

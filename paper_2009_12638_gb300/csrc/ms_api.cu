@@ -153,6 +153,7 @@ extern "C" void ms_default_opts(ms_opts* o) {
   o->persistent = 1;
   o->engine = 0;
   o->variant = -1;
+  o->inner_adapt = 0;
 }
 
 static std::vector<int> equal_cuts(int n, int p) {
@@ -262,6 +263,9 @@ static int check_opts(ms_grid* g, const ms_opts& o) {
   if (o.engine < 0 || o.engine > 2) return fail(g, MS_ERR_ARG, "opts.engine must be 0 (auto), 1 or 2");
   if (o.variant < -1 || o.variant >= ms::res_variant_count())
     return fail(g, MS_ERR_ARG, "opts.variant must be -1 (tuned) or 0..%d", ms::res_variant_count() - 1);
+  if (o.inner_adapt != 0 && o.inner_adapt != 1) return fail(g, MS_ERR_ARG, "opts.inner_adapt must be 0 or 1");
+  if (o.inner_adapt && o.mode != MS_MODE_SYNC)
+    return fail(g, MS_ERR_ARG, "opts.inner_adapt needs the synchronous mode (its controller runs between sweeps)");
   if (o.variant >= 0 && (o.precision != MS_PREC_MIXED || o.engine == 1))
     return fail(g, MS_ERR_ARG, "opts.variant selects a resident-engine layout: it needs precision MIXED and engine 0 or 2");
   return MS_OK;
@@ -269,7 +273,7 @@ static int check_opts(ms_grid* g, const ms_opts& o) {
 
 // Per-rhs bookkeeping arrays live after Ctl in the ctl buffer.
 struct CtlLayout {
-  size_t off_state, off_kfinal, off_inner, off_invb, off_norm, bytes;
+  size_t off_state, off_kfinal, off_inner, off_invb, off_norm, off_adapt, off_rtol, bytes;
 };
 static CtlLayout ctl_layout(int nrhs) {
   CtlLayout L;
@@ -284,6 +288,10 @@ static CtlLayout ctl_layout(int nrhs) {
   o += ((size_t)nrhs * sizeof(double) + 255) / 256 * 256;
   L.off_norm = o;
   o += ((size_t)nrhs * 2 * sizeof(double) + 255) / 256 * 256;
+  L.off_adapt = o;
+  o += ((size_t)nrhs * sizeof(AdaptState) + 255) / 256 * 256;
+  L.off_rtol = o;
+  o += ((size_t)nrhs * sizeof(double) + 255) / 256 * 256;
   L.bytes = o;
   return L;
 }
@@ -523,6 +531,7 @@ extern "C" int ms_gcg_solve(ms_grid* g, const double* f, const double* bnd, doub
     st->sweep_launches = 0;
     st->engine = 0;
     st->variant = -1;
+    st->inner_rtol_final = 0.0;
   }
   return status;
 }
@@ -645,10 +654,26 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
   unsigned long long* inner = reinterpret_cast<unsigned long long*>(ctlb + L.off_inner);
   double* invb = reinterpret_cast<double*>(ctlb + L.off_invb);
   double* norms = reinterpret_cast<double*>(ctlb + L.off_norm);
+  AdaptState* adapt = o.inner_adapt ? reinterpret_cast<AdaptState*>(ctlb + L.off_adapt) : nullptr;
+  double* rtol_rhs = reinterpret_cast<double*>(ctlb + L.off_rtol);
 
   MS_CUDA(g, cudaEventRecord(ev0, stream));
   MS_CUDA(g, cudaMemcpyAsync(g->tasks.p, tasks.data(), tasks.size() * sizeof(Task), cudaMemcpyHostToDevice, stream));
   MS_CUDA(g, cudaMemsetAsync(ctlb, 0, L.bytes, stream));
+  std::vector<AdaptState> h_adapt;
+  std::vector<double> h_rtol;
+  if (adapt) {
+    AdaptState a0{};
+    a0.c = kAdaptStart;
+    a0.rs = kAdaptWarmup;
+    a0.cur = kAdaptStart;
+    h_adapt.assign(g->nrhs, a0);
+    h_rtol.assign(g->nrhs, adapt_rung_rtol(kAdaptStart));
+    MS_CUDA(g, cudaMemcpyAsync(adapt, h_adapt.data(), h_adapt.size() * sizeof(AdaptState), cudaMemcpyHostToDevice,
+                               stream));
+    MS_CUDA(g, cudaMemcpyAsync(rtol_rhs, h_rtol.data(), h_rtol.size() * sizeof(double), cudaMemcpyHostToDevice,
+                               stream));
+  }
   // ||bhat|| per rhs (and the residual of x^0, unused here)
   rc = run_resid(g, f, bnd, x, norms, invb, stream);
   if (rc != MS_OK) return rc;
@@ -692,6 +717,7 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
     sa.inner_count = inner;
     sa.inv_bnorm = invb;
     sa.err = &ctl->err;
+    sa.inner_rtol_rhs = adapt ? rtol_rhs : nullptr;
     CheckArgs ca;
     ca.nrhs = g->nrhs;
     ca.ntasks = ntasks;
@@ -711,6 +737,10 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
     ca.err = &ctl->err;
     ca.use_cond = 0;
     ca.cond = 0;
+    ca.adapt = adapt;
+    ca.inner_rtol_rhs = rtol_rhs;
+    ca.inner_count = inner;
+    ca.npts = (double)g->npts();
 
     int chunk = o.check_every > 0 ? o.check_every : 4;
     int* h_flags = nullptr;  // all_done, err
@@ -809,7 +839,8 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
     mode_key.insert(mode_key.end(), {shape.variant, shape.cluster, shape.threads, shape.slots});
     Tuner::ModeMs* mm = nullptr;
     bool use_flow = o.persistent == 2;
-    if (o.persistent == 1 && shape.variant >= 0 && tail_waste > 0.05) {
+    if (o.inner_adapt) use_flow = false;  // the persistent kernel's in-kernel stop decision has no controller
+    else if (o.persistent == 1 && shape.variant >= 0 && tail_waste > 0.05) {
       mm = &g->tuner.mode_ms[mode_key];
       use_flow = mm->flow < 0.0 || (mm->sweep >= 0.0 && mm->flow < mm->sweep);
     }
@@ -1060,6 +1091,12 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
     st->slots = shape.slots;
     st->engine = shape.variant >= 0 ? 2 : 1;
     st->variant = shape.variant;
+    st->inner_rtol_final = o.inner_rtol;
+    if (adapt) {
+      std::vector<double> hr(g->nrhs);
+      MS_CUDA(g, cudaMemcpy(hr.data(), rtol_rhs, hr.size() * sizeof(double), cudaMemcpyDeviceToHost));
+      st->inner_rtol_final = *std::max_element(hr.begin(), hr.end());
+    }
   }
   return status;
 }

@@ -55,6 +55,37 @@ struct SweepArgs {
   unsigned long long* inner_count;  // [nrhs][2]: inner iterations, inner lattice updates
   const double* inv_bnorm;          // [nrhs] 1/||bhat|| (1 if bhat = 0): FP32 inner scaling
   int* err;
+  const double* inner_rtol_rhs;  // [nrhs] per-rhs inner tolerance (opts.inner_adapt) or null: inner_rtol
+};
+
+__host__ __device__ inline double sweep_inner_rtol(const SweepArgs& a, int rhs) {
+  return a.inner_rtol_rhs ? a.inner_rtol_rhs[rhs] : a.inner_rtol;
+}
+
+// Runtime adaptation of the inner tolerance (opts.inner_adapt), per rhs, run
+// by the check kernel after every sweep.  A ladder of relative inner
+// tolerances; rounds of 3 x kAdaptWindow sweeps run the centre rung, the next
+// looser and the next tighter one; each sweep's decrease of log(rho) is
+// charged to the rung it ran with, against its work (inner lattice updates
+// plus kAdaptSweepCost x points for the residual and update); the rung with
+// the largest decrease per work becomes the centre of the next round.  Every
+// input is deterministic (residuals and iteration counts, no clocks).
+constexpr int kAdaptRungs = 11;
+constexpr int kAdaptStart = 3;        // rung of the first sweeps (0.3)
+constexpr int kAdaptWindow = 8;       // sweeps per rung and round
+constexpr int kAdaptWarmup = 4;       // sweeps before the first round
+constexpr double kAdaptSweepCost = 12.0;  // residual + update, in inner iterations per point
+__host__ __device__ inline double adapt_rung_rtol(int r) {
+  constexpr double ladder[kAdaptRungs] = {0.8, 0.6, 0.45, 0.3, 0.2, 0.12, 0.07, 0.04, 0.02, 0.01, 1e-3};
+  return ladder[r < 0 ? 0 : (r >= kAdaptRungs ? kAdaptRungs - 1 : r)];
+}
+struct AdaptState {
+  int c;                       // centre rung of the current round
+  int rs;                      // first sweep of the current round
+  int cur;                     // rung of the next sweep
+  double lr_prev;              // log(rho_{k-1})
+  double cum_prev, cum_prev2;  // cumulative work at checks k-1 and k-2
+  double acc_d[3], acc_w[3];   // round sums per window: log-residual decrease, work
 };
 
 struct CheckArgs {
@@ -76,6 +107,10 @@ struct CheckArgs {
   int* err;
   int use_cond;                       // set the WHILE condition of the enclosing graph
   cudaGraphConditionalHandle cond;
+  AdaptState* adapt;                        // [nrhs] or null (no adaptation)
+  double* inner_rtol_rhs;                   // [nrhs] written for the next sweep when adapt != null
+  const unsigned long long* inner_count;    // [nrhs][2] cumulative inner iterations / lattice updates
+  double npts;                              // points per rhs
 };
 
 // Synchronous solve as one persistent "dataflow" launch (ms_resident.cu):

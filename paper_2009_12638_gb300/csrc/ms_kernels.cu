@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(NT, 1) sweep_kernel(const SweepArgs a) {
     if (rank == 0 && tid == 0) a.partial[t] = red0[0];
     if (residual_only) continue;
     // ---- 2. inner CG
-    const int m = block_cg<T, NT>(v, sl, red0[1], a.inner_rtol, a.inner_maxit, sm, rank, csize);
+    const int m = block_cg<T, NT>(v, sl, red0[1], sweep_inner_rtol(a, tk.rhs), a.inner_maxit, sm, rank, csize);
     // ---- 3. outer update into the other buffer
     double* __restrict__ xo = xout + rb;
     for (int c = tid; c < sl.plane; c += NT) {
@@ -115,6 +115,51 @@ __global__ void __launch_bounds__(NT, 1) sweep_kernel(const SweepArgs a) {
 
 // One CTA: per-rhs global norm from the block partials (fixed task order),
 // stop rule, bookkeeping for the next sweep.
+// Rung of sweep j under the round schedule of `st` (see AdaptState).
+__device__ __forceinline__ int adapt_rung_of(const AdaptState& st, int j) {
+  if (j < st.rs || j >= st.rs + 3 * kAdaptWindow) return st.c;
+  const int w = (j - st.rs) / kAdaptWindow;
+  const int r = st.c + (w == 1 ? -1 : (w == 2 ? 1 : 0));
+  return r < 0 ? 0 : (r >= kAdaptRungs ? kAdaptRungs - 1 : r);
+}
+
+// Controller step at check k for an rhs that continues: charge sweep k-1 to
+// its rung, close the round when its last sweep is charged, and set the
+// inner tolerance of sweep k+1.
+__device__ void adapt_step(const CheckArgs& a, int s, int k, double rho) {
+  AdaptState& st = a.adapt[s];
+  const double lr = log(fmax(rho, 1e-300));
+  const double cum = (double)a.inner_count[2 * s + 1] + kAdaptSweepCost * a.npts * (double)(k + 1);
+  if (k >= 1) {
+    const int j = k - 1;
+    if (j >= st.rs && j < st.rs + 3 * kAdaptWindow) {
+      const int w = (j - st.rs) / kAdaptWindow;
+      st.acc_d[w] += st.lr_prev - lr;
+      st.acc_w[w] += st.cum_prev - st.cum_prev2;
+      if (j == st.rs + 3 * kAdaptWindow - 1) {
+        int best = 0;
+        double be = -1e300;
+        for (int q = 0; q < 3; ++q) {
+          const double e = st.acc_w[q] > 0.0 ? st.acc_d[q] / st.acc_w[q] : -1e300;
+          if (e > be) {
+            be = e;
+            best = q;
+          }
+        }
+        const int rbest = adapt_rung_of(st, st.rs + best * kAdaptWindow);
+        for (int q = 0; q < 3; ++q) st.acc_d[q] = st.acc_w[q] = 0.0;
+        st.c = rbest;
+        st.rs = k + 1;
+      }
+    }
+  }
+  st.cum_prev2 = st.cum_prev;
+  st.cum_prev = cum;
+  st.lr_prev = lr;
+  st.cur = adapt_rung_of(st, k + 1);
+  a.inner_rtol_rhs[s] = adapt_rung_rtol(st.cur);
+}
+
 __global__ void check_kernel(const CheckArgs a) {
   const int k = *a.k_dev;
   __shared__ int timed_out;
@@ -138,6 +183,8 @@ __global__ void check_kernel(const CheckArgs a) {
     } else if (k >= a.outer_maxit || timed_out) {
       a.rhs_state[s] = kStopped;
       a.k_final[s] = k;
+    } else if (a.adapt) {
+      adapt_step(a, s, k, rho);
     }
   }
   __syncthreads();

@@ -156,7 +156,8 @@ __global__ void __launch_bounds__(NT, 1) res_sweep_kernel(const SweepArgs a, int
     if (rank == 0 && tid == 0) a.partial[t] = red0[0];
     int m = 0;
     if (!residual_only)
-      m = resident_cg<NT, KC, ZS, DS, QR>(r4, d4, g, s, sp, (float)red0[1], (float)a.inner_rtol, a.inner_maxit, rred,
+      m = resident_cg<NT, KC, ZS, DS, QR>(r4, d4, g, s, sp, (float)red0[1], (float)sweep_inner_rtol(a, tk.rhs),
+                                          a.inner_maxit, rred,
                                       rank, csize);
     // every cluster barrier of this task is behind us: with d in registers the
     // smem can be cleared for the next task right away (with d in smem, after the update)
@@ -495,7 +496,7 @@ __global__ void __launch_bounds__(NT, 1) res_flow_kernel(const FlowArgs fa, int 
       if (rank == 0 && tid == 0) st_rel_s32(fa.done_rel + t, kr + 1);
       continue;
     }
-    const int m = resident_cg<NT, KC, ZS, DS, QR>(r4, d4, g, s, sp, (float)red.tot[1], (float)a.inner_rtol,
+    const int m = resident_cg<NT, KC, ZS, DS, QR>(r4, d4, g, s, sp, (float)red.tot[1], (float)sweep_inner_rtol(a, tk.rhs),
                                               a.inner_maxit, rred, rank, csize);
     if constexpr (!DS) zero_smem<NT>(dyn4, smem_f4);
     double* xo = xout + rb;

@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(NT, 1) strip_sweep_kernel(const SweepArgs a) {
     if (rank == 0 && tid == 0) a.partial[t] = sm.tot[0];
     if (residual_only) continue;
     // ---- 2. inner CG
-    const int m = strip_cg<NT>(v, g, sm.tot[1], a.inner_rtol, a.inner_maxit, sm, rank, csize);
+    const int m = strip_cg<NT>(v, g, sm.tot[1], sweep_inner_rtol(a, tk.rhs), a.inner_maxit, sm, rank, csize);
     // ---- 3. outer update into the other buffer
     double* __restrict__ xo = xout + rb;
     for (int s0 = wbase; s0 < g.nstrips; s0 += NT) {
