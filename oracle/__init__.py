@@ -86,6 +86,9 @@ def _load():
         lib.or_solve.argtypes = [c_int, c_int, c_int, c_int, c_int, c_int, i, i, i, d, d, d, c_double, c_int,
                                  c_double, c_int, i, ll, d, d]
         lib.or_solve.restype = c_int
+        lib.or_solve_overlap.argtypes = [c_int, c_int, c_int, c_int, c_int, c_int, i, i, i, c_int, d, d, d, c_double,
+                                         c_int, c_double, c_int, i, ll, d, d]
+        lib.or_solve_overlap.restype = c_int
         lib.or_solve_delayed.argtypes = [c_int, c_int, c_int, c_int, c_int, c_int, i, i, i, d, d, d, c_double,
                                          c_int, c_double, c_int, c_int, i, i, d]
         lib.or_solve_delayed.restype = c_int
@@ -167,11 +170,13 @@ def _cuts(c):
 
 
 def solve(nx, ny, nz, cx, cy, cz, f=None, bnd=None, x0=None, inner_rtol=1e-6, inner_maxit=50,
-          outer_tol=1e-8, outer_maxit=100000, history=False):
+          outer_tol=1e-8, outer_maxit=100000, history=False, overlap=None):
     """Block Jacobi with inner CG for ONE right-hand side.
 
     Returns a dict: x (nz, ny, nx), status, outer_its, inner_its, rel_residual,
     and history (relative residual of every iterate x^0..x^K) if requested.
+    overlap: None = or_solve; o >= 0 = or_solve_overlap with blocks extended
+    by o points per face (o = 0 gives or_solve's result).
     """
     cx, cy, cz = _cuts(cx), _cuts(cy), _cuts(cz)
     px, py, pz = len(cx) - 1, len(cy) - 1, len(cz) - 1
@@ -184,9 +189,15 @@ def solve(nx, ny, nz, cx, cy, cz, f=None, bnd=None, x0=None, inner_rtol=1e-6, in
     inner = ctypes.c_longlong(0)
     rel = ctypes.c_double(0.0)
     hist = np.zeros(outer_maxit + 1) if history else None
-    st = _load().or_solve(nx, ny, nz, px, py, pz, _ip(cx), _ip(cy), _ip(cz), _dp(f), _dp(bnd), _dp(x),
-                          float(inner_rtol), int(inner_maxit), float(outer_tol), int(outer_maxit),
-                          ctypes.byref(outer), ctypes.byref(inner), _dp(hist), ctypes.byref(rel))
+    if overlap is None:
+        st = _load().or_solve(nx, ny, nz, px, py, pz, _ip(cx), _ip(cy), _ip(cz), _dp(f), _dp(bnd), _dp(x),
+                              float(inner_rtol), int(inner_maxit), float(outer_tol), int(outer_maxit),
+                              ctypes.byref(outer), ctypes.byref(inner), _dp(hist), ctypes.byref(rel))
+    else:
+        st = _load().or_solve_overlap(nx, ny, nz, px, py, pz, _ip(cx), _ip(cy), _ip(cz), int(overlap), _dp(f),
+                                      _dp(bnd), _dp(x), float(inner_rtol), int(inner_maxit), float(outer_tol),
+                                      int(outer_maxit), ctypes.byref(outer), ctypes.byref(inner), _dp(hist),
+                                      ctypes.byref(rel))
     if st == ERR_ARG:
         raise ValueError("oracle rejected the arguments")
     out = dict(x=x, status=int(st), outer_its=int(outer.value), inner_its=int(inner.value),

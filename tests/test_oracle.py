@@ -355,3 +355,97 @@ def test_delayed_converges_to_lu(oracle_mod):
     A = kron_laplacian(n, n, n).toarray()
     x_lu = np.linalg.solve(A, bhat_independent(n, n, n, None, g).ravel())
     assert np.abs(res["x"].ravel() - x_lu).max() <= np.linalg.cond(A) * 1e-10 * np.abs(x_lu).max()
+
+
+# ---------------------------------------------------------------- overlapping blocks
+def _boxes(cuts, n, o):
+    """Owned and extended index ranges per block along one axis."""
+    c = np.asarray(cuts)
+    return [(c[i], c[i + 1], max(0, c[i] - o), min(n, c[i + 1] + o)) for i in range(len(c) - 1)]
+
+
+def dense_overlap_sweeps(nx, ny, nz, cx, cy, cz, o, f, g, sweeps):
+    """Brute force (no oracle code): every block solves its extended-box system
+    A[E,E] d = (b - A x)[E] exactly (dense LU) and x takes d on the points the
+    block owns."""
+    A = kron_laplacian(nx, ny, nz).toarray()
+    b = bhat_independent(nx, ny, nz, f, g).ravel()
+    idx = np.arange(nx * ny * nz).reshape(nz, ny, nx)
+    x = np.zeros(A.shape[0])
+    out = []
+    for _ in range(sweeps):
+        r = b - A @ x
+        xn = x.copy()
+        for (wz0, wz1, ez0, ez1) in _boxes(cz, nz, o):
+            for (wy0, wy1, ey0, ey1) in _boxes(cy, ny, o):
+                for (wx0, wx1, ex0, ex1) in _boxes(cx, nx, o):
+                    E = idx[ez0:ez1, ey0:ey1, ex0:ex1].ravel()
+                    d = np.linalg.solve(A[np.ix_(E, E)], r[E]).reshape(ez1 - ez0, ey1 - ey0, ex1 - ex0)
+                    W = idx[wz0:wz1, wy0:wy1, wx0:wx1].ravel()
+                    xn[W] = x[W] + d[wz0 - ez0:wz1 - ez0, wy0 - ey0:wy1 - ey0, wx0 - ex0:wx1 - ex0].ravel()
+        x = xn
+        out.append(x.copy())
+    return out
+
+
+def test_overlap_zero_is_block_jacobi(oracle_mod):
+    """Overlap 0 is the non-overlapping method, bit for bit."""
+    nx, ny, nz = 11, 9, 7
+    r = rng(20)
+    g = r.standard_normal(inputs.boundary_size(nx, ny, nz))
+    f = r.standard_normal((nz, ny, nx))
+    cuts = ([0, 4, 11], [0, 3, 6, 9], [0, 7])
+    a = oracle_mod.solve(nx, ny, nz, *cuts, f=f, bnd=g, inner_maxit=7, outer_tol=1e-9)
+    b = oracle_mod.solve(nx, ny, nz, *cuts, f=f, bnd=g, inner_maxit=7, outer_tol=1e-9, overlap=0)
+    np.testing.assert_array_equal(a["x"], b["x"])
+    assert (a["outer_its"], a["inner_its"]) == (b["outer_its"], b["inner_its"])
+
+
+@pytest.mark.parametrize("o", [1, 2, 3])
+@pytest.mark.parametrize("cuts", [((0, 3, 6), (0, 2, 5), (0, 2, 4)), ((0, 2, 4, 6), (0, 5), (0, 1, 4))])
+def test_overlap_sweeps_match_dense_extended_solves(oracle_mod, o, cuts):
+    cx, cy, cz = (list(c) for c in cuts)
+    nx, ny, nz = cx[-1], cy[-1], cz[-1]
+    r = rng(21 + o)
+    g = r.standard_normal(inputs.boundary_size(nx, ny, nz))
+    f = r.standard_normal((nz, ny, nx))
+    ref = dense_overlap_sweeps(nx, ny, nz, cx, cy, cz, o, f, g, 3)
+    for k in range(1, 4):
+        res = oracle_mod.solve(nx, ny, nz, cx, cy, cz, f=f, bnd=g, inner_rtol=1e-15, inner_maxit=2000,
+                               outer_tol=0.0, outer_maxit=k, overlap=o)
+        np.testing.assert_allclose(res["x"].ravel(), ref[k - 1], rtol=1e-10, atol=1e-11)
+
+
+def test_overlap_covering_the_grid_solves_in_one_sweep(oracle_mod):
+    """When every extended box is the whole grid, one sweep with exact inner
+    solves is one exact solve per block: the LU solution."""
+    nx, ny, nz = 6, 5, 4
+    r = rng(25)
+    g = r.standard_normal(inputs.boundary_size(nx, ny, nz))
+    A = kron_laplacian(nx, ny, nz).toarray()
+    x_lu = np.linalg.solve(A, bhat_independent(nx, ny, nz, None, g).ravel())
+    res = oracle_mod.solve(nx, ny, nz, [0, 3, 6], [0, 2, 5], [0, 2, 4], bnd=g, inner_rtol=1e-15, inner_maxit=2000,
+                           outer_tol=0.0, outer_maxit=1, overlap=6)
+    np.testing.assert_allclose(res["x"].ravel(), x_lu, rtol=1e-10, atol=1e-11)
+
+
+def test_overlap_converges_to_lu(oracle_mod):
+    nx, ny, nz = 8, 7, 6
+    r = rng(26)
+    g = r.standard_normal(inputs.boundary_size(nx, ny, nz))
+    f = r.standard_normal((nz, ny, nx))
+    A = kron_laplacian(nx, ny, nz).toarray()
+    x_lu = np.linalg.solve(A, bhat_independent(nx, ny, nz, f, g).ravel())
+    res = oracle_mod.solve(nx, ny, nz, [0, 4, 8], [0, 3, 7], [0, 3, 6], f=f, bnd=g, outer_tol=1e-12, overlap=2)
+    assert res["status"] == 0
+    assert np.linalg.norm(res["x"].ravel() - x_lu) <= np.linalg.cond(A) * 1e-12 * np.linalg.norm(x_lu)
+
+
+def test_small_overlap_needs_fewer_outer_sweeps(oracle_mod):
+    """Section 3.2: an overlap of one to a few elements lowers the outer
+    iteration count (2341 -> 1771 -> 1330 for overlaps 0, 1, 5 in the paper)."""
+    n = 24
+    c = inputs.equal_cuts(n, 4)
+    g = rng(27).uniform(-1, 1, inputs.boundary_size(n, n, n))
+    its = [oracle_mod.solve(n, n, n, c, c, c, bnd=g, outer_tol=1e-8, overlap=o)["outer_its"] for o in (0, 1, 2)]
+    assert its[1] < its[0] and its[2] < its[1]
