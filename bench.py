@@ -326,8 +326,9 @@ def main():
         comp = {}
         for name, extra in [("fp64_sync", dict(precision="fp64", mode="sync")),
                             ("mixed_async", dict(precision="mixed", mode="async")),
-                            ("mixed_sync_adaptive_inner", dict(precision="mixed", mode="sync", inner_adapt=True))]:
-            if extra["precision"] == args.precision and extra["mode"] == args.mode and "inner_adapt" not in extra:
+                            ("mixed_sync_adaptive_inner", dict(precision="mixed", mode="sync", inner_adapt=True)),
+                            ("mixed_sync_overlap5", dict(precision="mixed", mode="sync", overlap=5))]:
+            if extra["precision"] == args.precision and extra["mode"] == args.mode and len(extra) == 2:
                 continue
             x.zero_()
             torch.cuda.synchronize(dev)

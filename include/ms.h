@@ -106,6 +106,13 @@ typedef struct {
                             residual and update), tries the neighbouring tolerances of a ladder
                             (0.8 ... 1e-3) in rounds of 8 sweeps each and keeps the most efficient;
                             inner_maxit still caps every inner solve.  Deterministic (no clocks). */
+  int overlap;           /* sync mode: overlapping blocks (section 3.2), o >= 0 points per face
+                            (default 0).  Block i solves on its box extended by o points on every
+                            face (clipped to the grid) with zero Dirichlet data outside the box;
+                            x^{k+1} takes block i's result on the points block i owns (a
+                            multisplitting with weight 1 on owned points, 0 on overlapped ones);
+                            the global residual counts every point once.  Runs on the streaming
+                            engine (engine 0 or 1). */
 } ms_opts;
 
 typedef struct {

@@ -52,6 +52,7 @@ class Opts(ctypes.Structure):
         ("engine", ctypes.c_int),
         ("variant", ctypes.c_int),
         ("inner_adapt", ctypes.c_int),
+        ("overlap", ctypes.c_int),
     ]
 
 

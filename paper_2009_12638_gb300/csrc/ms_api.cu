@@ -154,6 +154,7 @@ extern "C" void ms_default_opts(ms_opts* o) {
   o->engine = 0;
   o->variant = -1;
   o->inner_adapt = 0;
+  o->overlap = 0;
 }
 
 static std::vector<int> equal_cuts(int n, int p) {
@@ -223,20 +224,27 @@ extern "C" int ms_get_cuts(ms_grid* g, int* cx, int* cy, int* cz) {
 
 // Tasks: every (block, rhs), largest blocks first (longest-processing-time
 // order for the dynamic queue), ties in (rhs, block id) order.
-static std::vector<Task> build_tasks(const ms_grid* g, long long* max_pts) {
+// Tasks of the partition; with overlap o > 0 every box is the block extended
+// by o points on each face (clipped to the grid), the owned range marking the
+// block itself (section 3.2's overlapping blocks).
+static std::vector<Task> build_tasks(const ms_grid* g, long long* max_pts, int overlap = 0) {
   std::vector<Task> ts;
   long long mx = 0;
+  auto ext = [&](int lo, int hi, int n, int* o0, int* len, int* w0, int* w1) {
+    const int e0 = std::max(0, lo - overlap), e1 = std::min(n, hi + overlap);
+    *o0 = e0;
+    *len = e1 - e0;
+    *w0 = lo - e0;
+    *w1 = hi - e0;
+  };
   for (int s = 0; s < g->nrhs; ++s)
     for (int bk = 0; bk < g->pz; ++bk)
       for (int bj = 0; bj < g->py; ++bj)
         for (int bi = 0; bi < g->px; ++bi) {
           Task t;
-          t.ox = g->cx[bi];
-          t.oy = g->cy[bj];
-          t.oz = g->cz[bk];
-          t.bx = g->cx[bi + 1] - t.ox;
-          t.by = g->cy[bj + 1] - t.oy;
-          t.bz = g->cz[bk + 1] - t.oz;
+          ext(g->cx[bi], g->cx[bi + 1], g->nx, &t.ox, &t.bx, &t.wx0, &t.wx1);
+          ext(g->cy[bj], g->cy[bj + 1], g->ny, &t.oy, &t.by, &t.wy0, &t.wy1);
+          ext(g->cz[bk], g->cz[bk + 1], g->nz, &t.oz, &t.bz, &t.wz0, &t.wz1);
           t.rhs = s;
           t.block = bi + g->px * (bj + g->py * bk);
           mx = std::max(mx, (long long)t.bx * t.by * t.bz);
@@ -264,6 +272,11 @@ static int check_opts(ms_grid* g, const ms_opts& o) {
   if (o.variant < -1 || o.variant >= ms::res_variant_count())
     return fail(g, MS_ERR_ARG, "opts.variant must be -1 (tuned) or 0..%d", ms::res_variant_count() - 1);
   if (o.inner_adapt != 0 && o.inner_adapt != 1) return fail(g, MS_ERR_ARG, "opts.inner_adapt must be 0 or 1");
+  if (o.overlap < 0) return fail(g, MS_ERR_ARG, "opts.overlap must be >= 0");
+  if (o.overlap > 0 && o.mode != MS_MODE_SYNC)
+    return fail(g, MS_ERR_ARG, "opts.overlap needs the synchronous mode (the asynchronous faces are one layer deep)");
+  if (o.overlap > 0 && o.engine == 2)
+    return fail(g, MS_ERR_ARG, "opts.overlap runs on the streaming engine (engine 0 or 1)");
   if (o.inner_adapt && o.mode != MS_MODE_SYNC)
     return fail(g, MS_ERR_ARG, "opts.inner_adapt needs the synchronous mode (its controller runs between sweeps)");
   if (o.variant >= 0 && (o.precision != MS_PREC_MIXED || o.engine == 1))
@@ -585,7 +598,7 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
   const int prec = o.precision == MS_PREC_MIXED ? 1 : 0;
   const size_t esz = prec ? sizeof(float) : sizeof(double);
   long long maxpts = 0;
-  std::vector<Task> tasks = build_tasks(g, &maxpts);
+  std::vector<Task> tasks = build_tasks(g, &maxpts, o.overlap);
   const int ntasks = (int)tasks.size();
   const long long npts = g->npts();
   const size_t xbytes = (size_t)g->nrhs * npts * sizeof(double);
@@ -604,7 +617,9 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
   // launch shape: an explicit request, a shape measured earlier for this
   // problem, or -- sync mode -- candidates measured on the first sweeps
   std::vector<LaunchShape> all;
-  int rc = list_shapes(g->tuner, prec, o.mode, o.variant >= 0 ? 2 : o.engine, tasks, maxpts, o.cluster, o.threads,
+  // overlapping blocks run on the streaming engines (the resident layouts keep no owned range)
+  int rc = list_shapes(g->tuner, prec, o.mode, o.variant >= 0 ? 2 : (o.overlap > 0 ? 1 : o.engine), tasks, maxpts,
+                       o.cluster, o.threads,
                        o.slots, o.variant, &all);
   if (rc != 0) return fail(g, MS_ERR_CUDA, "ms_solve: no launchable shape (%s)", cudaGetErrorString((cudaError_t)rc));
   LaunchShape shape = all.front();
@@ -839,7 +854,9 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
     mode_key.insert(mode_key.end(), {shape.variant, shape.cluster, shape.threads, shape.slots});
     Tuner::ModeMs* mm = nullptr;
     bool use_flow = o.persistent == 2;
-    if (o.inner_adapt) use_flow = false;  // the persistent kernel's in-kernel stop decision has no controller
+    // the persistent kernel's in-kernel stop decision has no controller, and its
+    // six-neighbour dependencies do not cover the diagonal neighbours an overlapping box reads
+    if (o.inner_adapt || o.overlap > 0) use_flow = false;
     else if (o.persistent == 1 && shape.variant >= 0 && tail_waste > 0.05) {
       mm = &g->tuner.mode_ms[mode_key];
       use_flow = mm->flow < 0.0 || (mm->sweep >= 0.0 && mm->flow < mm->sweep);
@@ -1075,7 +1092,10 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
     // decides the stop), async mode one per block visit (st->lups on entry)
     long long resid_lups = 0;
     if (o.mode == MS_MODE_SYNC) {
-      for (int r = 0; r < g->nrhs; ++r) resid_lups += ((long long)h_kfinal[r] + 1) * npts;
+      long long box_pts = 0;  // residual points per rhs and sweep (the boxes, overlap included)
+      for (const Task& t : tasks)
+        if (t.rhs == 0) box_pts += (long long)t.bx * t.by * t.bz;
+      for (int r = 0; r < g->nrhs; ++r) resid_lups += ((long long)h_kfinal[r] + 1) * box_pts;
     } else {
       resid_lups = st->lups;
     }

@@ -13,9 +13,19 @@ constexpr int kMaxCluster = 16;
 
 // One unit of outer work: block `block` of right-hand side `rhs`.
 // (ox, oy, oz) is the block origin in the grid, (bx, by, bz) its edge lengths.
+// One (block, rhs) pair.  (ox, oy, oz) + (bx, by, bz) is the box the inner
+// CG solves on: the block itself, or with overlapping blocks the block
+// extended by the overlap on every face (clipped to the grid).  The block's
+// own points are [wx0, wx1) x [wy0, wy1) x [wz0, wz1) in box coordinates:
+// only they count towards the global residual and only they are updated.
 struct Task {
   int ox, oy, oz, bx, by, bz, rhs, block;
+  int wx0, wx1, wy0, wy1, wz0, wz1;
 };
+
+__host__ __device__ inline bool owns(const Task& t, int lx, int ly, int lz) {
+  return lx >= t.wx0 && lx < t.wx1 && ly >= t.wy0 && ly < t.wy1 && lz >= t.wz0 && lz < t.wz1;
+}
 
 struct Geo {
   int nx, ny, nz, nrhs;

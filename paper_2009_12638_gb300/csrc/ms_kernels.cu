@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(NT, 1) sweep_kernel(const SweepArgs a) {
           nbr_sums(g, xr, br, gx, gy, gz, gi, si, so);
           const double bh = fr ? fr[gi] + so : so;
           const double rr = bh - (6.0 * xr[gi] - si);
-          s_loc += rr * rr;
+          if (owns(tk, c % tk.bx, c / tk.bx, z)) s_loc += rr * rr;  // the global norm counts owned points
           const T rt = (T)(rr * scale);
           v.r[z * sl.plane + c] = rt;
           g_loc += rt * rt;
@@ -97,11 +97,12 @@ __global__ void __launch_bounds__(NT, 1) sweep_kernel(const SweepArgs a) {
     if (residual_only) continue;
     // ---- 2. inner CG
     const int m = block_cg<T, NT>(v, sl, red0[1], sweep_inner_rtol(a, tk.rhs), a.inner_maxit, sm, rank, csize);
-    // ---- 3. outer update into the other buffer
+    // ---- 3. outer update into the other buffer (owned points only)
     double* __restrict__ xo = xout + rb;
     for (int c = tid; c < sl.plane; c += NT) {
       const int gx = tk.ox + c % tk.bx, gy = tk.oy + c / tk.bx;
       for (int z = sl.z0; z < sl.z1; ++z) {
+        if (!owns(tk, c % tk.bx, c / tk.bx, z)) continue;
         const long long gi = (long long)(tk.oz + z) * nxy + (long long)gy * g.nx + gx;
         xo[gi] = (m > 0) ? xr[gi] + (double)v.d[z * sl.plane + c] * unscale : xr[gi];
       }
@@ -113,8 +114,6 @@ __global__ void __launch_bounds__(NT, 1) sweep_kernel(const SweepArgs a) {
   }
 }
 
-// One CTA: per-rhs global norm from the block partials (fixed task order),
-// stop rule, bookkeeping for the next sweep.
 // Rung of sweep j under the round schedule of `st` (see AdaptState).
 __device__ __forceinline__ int adapt_rung_of(const AdaptState& st, int j) {
   if (j < st.rs || j >= st.rs + 3 * kAdaptWindow) return st.c;
@@ -160,6 +159,9 @@ __device__ void adapt_step(const CheckArgs& a, int s, int k, double rho) {
   a.inner_rtol_rhs[s] = adapt_rung_rtol(st.cur);
 }
 
+// One CTA: per-rhs global norm from the block partials (fixed task order),
+// stop rule, bookkeeping for the next sweep (and the inner-tolerance
+// controller when enabled).
 __global__ void check_kernel(const CheckArgs a) {
   const int k = *a.k_dev;
   __shared__ int timed_out;

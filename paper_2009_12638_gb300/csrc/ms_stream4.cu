@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(NT, 1) strip_sweep_kernel(const SweepArgs a) {
               nbr_sums(G, xr, br, gx0 + l, gy, gz, gi, si, so);
               const double bh = fr ? fr[gi] + so : so;
               const double rr = bh - (6.0 * xr[gi] - si);
-              s_loc += rr * rr;
+              if (owns(tk, 4 * s.xs + l, s.y, z)) s_loc += rr * rr;  // the global norm counts owned points
               rv[l] = (float)(rr * scale);
             }
           }
@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(NT, 1) strip_sweep_kernel(const SweepArgs a) {
     if (residual_only) continue;
     // ---- 2. inner CG
     const int m = strip_cg<NT>(v, g, sm.tot[1], sweep_inner_rtol(a, tk.rhs), a.inner_maxit, sm, rank, csize);
-    // ---- 3. outer update into the other buffer
+    // ---- 3. outer update into the other buffer (owned points only)
     double* __restrict__ xo = xout + rb;
     for (int s0 = wbase; s0 < g.nstrips; s0 += NT) {
       const StripPos s = strip_pos(g, s0 + lane, lane);
@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(NT, 1) strip_sweep_kernel(const SweepArgs a) {
         const float dv[4] = {d.x, d.y, d.z, d.w};
 #pragma unroll
         for (int l = 0; l < 4; ++l)
-          if (s.msk & (1u << l)) xo[gi0 + l] = xr[gi0 + l] + (double)dv[l] * unscale;
+          if ((s.msk & (1u << l)) && owns(tk, 4 * s.xs + l, s.y, z)) xo[gi0 + l] = xr[gi0 + l] + (double)dv[l] * unscale;
       }
     }
     if (rank == 0 && tid == 0 && m > 0) {

@@ -47,9 +47,9 @@ def test_ctypes_structs_match_c_layout(tmp_path):
 #include <stddef.h>
 #include "ms.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(ms_opts), offsetof(ms_opts, outer_tol), offsetof(ms_opts, res_hist),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(ms_opts), offsetof(ms_opts, outer_tol), offsetof(ms_opts, res_hist),
          offsetof(ms_opts, slow_ns), offsetof(ms_opts, time_limit_ms), offsetof(ms_opts, variant),
-         offsetof(ms_opts, inner_adapt));
+         offsetof(ms_opts, inner_adapt), offsetof(ms_opts, overlap));
   printf("%zu %zu %zu %zu %zu %zu\n", sizeof(ms_stats), offsetof(ms_stats, lups), offsetof(ms_stats, per_rhs_rel),
          offsetof(ms_stats, slots), offsetof(ms_stats, variant), offsetof(ms_stats, inner_rtol_final));
   return 0;
@@ -61,7 +61,7 @@ int main(void) {
     O, S = _lib.Opts, _lib.Stats
     assert [int(v) for v in a.split()] == [ctypes.sizeof(O), O.outer_tol.offset, O.res_hist.offset,
                                           O.slow_ns.offset, O.time_limit_ms.offset, O.variant.offset,
-                                          O.inner_adapt.offset]
+                                          O.inner_adapt.offset, O.overlap.offset]
     assert [int(v) for v in b.split()] == [ctypes.sizeof(S), S.lups.offset, S.per_rhs_rel.offset, S.slots.offset,
                                           S.variant.offset, S.inner_rtol_final.offset]
 
@@ -144,7 +144,7 @@ def test_solve_rejects_bad_arguments_before_device_work(lib):
         dummy = ctypes.c_void_p(16)  # never dereferenced: options are checked first
         for field, value in [("mode", 7), ("precision", 3), ("inner_maxit", -1), ("threads", 100),
                              ("cluster", 17), ("outer_tol", -1.0), ("time_limit_ms", -5.0), ("variant", -2),
-                             ("variant", 10000), ("inner_adapt", 2)]:
+                             ("variant", 10000), ("inner_adapt", 2), ("overlap", -1)]:
             o2 = _lib.Opts()
             lib.ms_default_opts(ctypes.byref(o2))
             setattr(o2, field, value)
@@ -154,6 +154,12 @@ def test_solve_rejects_bad_arguments_before_device_work(lib):
         lib.ms_default_opts(ctypes.byref(o2))
         o2.inner_adapt, o2.mode = 1, 1
         assert lib.ms_solve(h, None, None, dummy, ctypes.byref(o2), None, None) == _lib.MS_ERR_ARG
+        # overlapping blocks: sync mode and the streaming engine only
+        for mode, eng in [(1, 0), (0, 2)]:
+            o2 = _lib.Opts()
+            lib.ms_default_opts(ctypes.byref(o2))
+            o2.overlap, o2.mode, o2.engine = 1, mode, eng
+            assert lib.ms_solve(h, None, None, dummy, ctypes.byref(o2), None, None) == _lib.MS_ERR_ARG
         # a resident layout with FP64 or the streaming engine is rejected before device work
         for prec, eng in [(0, 0), (1, 1)]:
             o2 = _lib.Opts()
