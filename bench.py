@@ -73,6 +73,9 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--mode", default="sync", choices=["sync", "async"])
+    ap.add_argument("--engine", default="auto", choices=["auto", "streaming", "resident"],
+                    help="inner-CG engine (default: the autotuner's choice)")
+    ap.add_argument("--overlap", type=int, default=0, help="overlapping blocks: points per face (sync mode)")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64-sync and async comparison solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--sweeps", type=int, default=0,
@@ -219,7 +222,7 @@ def main():
     grid.partition(len(cfg["cx"]) - 1, len(cfg["cy"]) - 1, len(cfg["cz"]) - 1, cfg["cx"], cfg["cy"], cfg["cz"])
     bnd = torch.from_numpy(bnd_np).to(dev)
     x = torch.zeros(grid.shape, dtype=torch.float64, device=dev)
-    opts = dict(cfg["opts"], precision=args.precision, mode=args.mode)
+    opts = dict(cfg["opts"], precision=args.precision, mode=args.mode, engine=args.engine, overlap=args.overlap)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
     stream = torch.cuda.current_stream(dev)
 
@@ -296,7 +299,7 @@ def main():
     except Exception:
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
-    kname = "res_sweep_kernel" if sp.engine == 2 else "sweep_kernel"
+    kname = {True: "res_sweep_kernel", False: "strip_sweep_kernel" if sp.variant == -2 else "sweep_kernel"}[sp.variant >= 0]
     traffic, _ = measured_traffic(kname)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": kname, "per_launch_ms": per_launch_ms,
@@ -312,7 +315,8 @@ def main():
            "data": "synthetic",
            "config": {"workload": f"{args.workload}: 256^3 Laplace 7-point, 4x4x4 blocks of 64^3, boundary iid "
                                   "U(-1,1) seed 2009, x0=0, inner CG <=50 its rtol 1e-6, outer rel tol 1e-8",
-                      "precision": args.precision, "mode": args.mode,
+                      "precision": args.precision, "mode": args.mode, "engine": args.engine,
+                      "overlap": args.overlap,
                       "launch_shape": {"cluster": st0.cluster, "threads": st0.threads, "slots": st0.slots},
                       "kernel_source_hash": kernel_source_hash(),
                       "l2": "flushed (256 MB write) between timed solves"},

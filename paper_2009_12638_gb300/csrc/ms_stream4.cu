@@ -105,14 +105,19 @@ __device__ int strip_cg(const CgVecs<float>& v, const StripGeo& g, double gamma0
   for (;;) {
     const float beta = sm.beta;
     // ---------------- pass A: p_new at the strip and its neighbours, q = A_ii p_new, eta = p.q
+    // (within a pass the vectors are distinct: pass A reads r and p_old and writes
+    // p_new, so the next planes' loads may move ahead of this plane's store)
+    const float* __restrict__ rA = v.r;
+    const float* __restrict__ poA = po;
+    float* __restrict__ pnA = pn;
     float eta_loc = 0.f;
     for (int s0 = wbase; s0 < g.nstrips; s0 += NT) {
       const StripPos s = strip_pos(g, s0 + lane, lane);
       auto pnew = [&](long long i) -> float4 {  // i: float index of a strip start
-        const float4 r = ld4(v.r + i);
-        return first ? r : fma4(beta, ld4(po + i), r);
+        const float4 r = ld4(rA + i);
+        return first ? r : fma4(beta, ld4(poA + i), r);
       };
-      auto pnew_s = [&](long long i) -> float { return first ? v.r[i] : fmaf(beta, po[i], v.r[i]); };
+      auto pnew_s = [&](long long i) -> float { return first ? rA[i] : fmaf(beta, poA[i], rA[i]); };
       float4 zm = (s.has && g.z0 > 0 && g.z0 < g.z1) ? pnew((long long)(g.z0 - 1) * g.plane + s.off) : zero4();
       float4 c = (s.has && g.z0 < g.z1) ? pnew((long long)g.z0 * g.plane + s.off) : zero4();
       for (int z = g.z0; z < g.z1; ++z) {
@@ -125,7 +130,7 @@ __device__ int strip_cg(const CgVecs<float>& v, const StripGeo& g, double gamma0
         const float xl = s.lin ? l_sh : ((s.has && s.xs > 0) ? pnew_s(base + s.off - 1) : 0.f);
         const float xr = s.rin ? r_sh : ((s.has && s.xs + 1 < g.spr) ? pnew_s(base + s.off + 4) : 0.f);
         const float4 q = msk4(stencil_strip(c, zm, zp, ym, yp, xl, xr), s.msk);
-        if (s.has) st4(pn + base + s.off, c);
+        if (s.has) st4(pnA + base + s.off, c);
         eta_loc += dot4f(c, q);
         zm = c;
         c = zp;
@@ -138,27 +143,31 @@ __device__ int strip_cg(const CgVecs<float>& v, const StripGeo& g, double gamma0
     if (sm.done) break;
     const float alpha = sm.alpha;
     // ---------------- pass B: q = A_ii p_new again, d += alpha p, r -= alpha q, gamma = r.r
+    // (reads p_new; d and r are read and written at the strip itself only)
+    const float* __restrict__ pnB = pn;
+    float* __restrict__ dB = v.d;
+    float* __restrict__ rB = v.r;
     float g_loc = 0.f;
     for (int s0 = wbase; s0 < g.nstrips; s0 += NT) {
       const StripPos s = strip_pos(g, s0 + lane, lane);
-      float4 zm = (s.has && g.z0 > 0 && g.z0 < g.z1) ? ld4(pn + (long long)(g.z0 - 1) * g.plane + s.off) : zero4();
-      float4 c = (s.has && g.z0 < g.z1) ? ld4(pn + (long long)g.z0 * g.plane + s.off) : zero4();
+      float4 zm = (s.has && g.z0 > 0 && g.z0 < g.z1) ? ld4(pnB + (long long)(g.z0 - 1) * g.plane + s.off) : zero4();
+      float4 c = (s.has && g.z0 < g.z1) ? ld4(pnB + (long long)g.z0 * g.plane + s.off) : zero4();
       for (int z = g.z0; z < g.z1; ++z) {
         const long long base = (long long)z * g.plane;
-        const float4 zp = (s.has && z + 1 < g.bz) ? ld4(pn + base + g.plane + s.off) : zero4();
-        const float4 ym = (s.has && s.y > 0) ? ld4(pn + base + s.off - g.pitch) : zero4();
-        const float4 yp = (s.has && s.y + 1 < g.by) ? ld4(pn + base + s.off + g.pitch) : zero4();
+        const float4 zp = (s.has && z + 1 < g.bz) ? ld4(pnB + base + g.plane + s.off) : zero4();
+        const float4 ym = (s.has && s.y > 0) ? ld4(pnB + base + s.off - g.pitch) : zero4();
+        const float4 yp = (s.has && s.y + 1 < g.by) ? ld4(pnB + base + s.off + g.pitch) : zero4();
         const float l_sh = __shfl_up_sync(0xffffffffu, c.w, 1);
         const float r_sh = __shfl_down_sync(0xffffffffu, c.x, 1);
-        const float xl = s.lin ? l_sh : ((s.has && s.xs > 0) ? pn[base + s.off - 1] : 0.f);
-        const float xr = s.rin ? r_sh : ((s.has && s.xs + 1 < g.spr) ? pn[base + s.off + 4] : 0.f);
+        const float xl = s.lin ? l_sh : ((s.has && s.xs > 0) ? pnB[base + s.off - 1] : 0.f);
+        const float xr = s.rin ? r_sh : ((s.has && s.xs + 1 < g.spr) ? pnB[base + s.off + 4] : 0.f);
         const float4 q = msk4(stencil_strip(c, zm, zp, ym, yp, xl, xr), s.msk);
         if (s.has) {
           const long long i = base + s.off;
-          const float4 d = first ? zero4() : ld4(v.d + i);
-          st4(v.d + i, fma4(alpha, c, d));
-          const float4 r = fma4(-alpha, q, ld4(v.r + i));
-          st4(v.r + i, r);
+          const float4 d = first ? zero4() : ld4(dB + i);
+          st4(dB + i, fma4(alpha, c, d));
+          const float4 r = fma4(-alpha, q, ld4(rB + i));
+          st4(rB + i, r);
           g_loc += dot4f(r, r);
         }
         zm = c;
