@@ -89,6 +89,11 @@ def _load():
         lib.or_solve_overlap.argtypes = [c_int, c_int, c_int, c_int, c_int, c_int, i, i, i, c_int, d, d, d, c_double,
                                          c_int, c_double, c_int, i, ll, d, d]
         lib.or_solve_overlap.restype = c_int
+        lib.or_solve_ex.argtypes = [c_int, c_int, c_int, c_int, c_int, c_int, i, i, i, c_int, c_int, d, d, d, c_double,
+                                    c_int, c_double, c_int, i, ll, d, d]
+        lib.or_solve_ex.restype = c_int
+        lib.or_block_gmres.argtypes = [c_int, c_int, c_int, d, d, c_double, c_int, c_int]
+        lib.or_block_gmres.restype = c_int
         lib.or_solve_delayed.argtypes = [c_int, c_int, c_int, c_int, c_int, c_int, i, i, i, d, d, d, c_double,
                                          c_int, c_double, c_int, c_int, i, i, d]
         lib.or_solve_delayed.restype = c_int
@@ -165,18 +170,28 @@ def block_cg(r: np.ndarray, inner_rtol: float, inner_maxit: int):
     return d, r, int(m)
 
 
+def block_gmres(r: np.ndarray, inner_rtol: float, inner_maxit: int, restart: int):
+    """Restarted GMRES on one block system A_ii d = r from d = 0; returns (d, r_final, iterations)."""
+    r = _f64(r).copy()
+    bz, by, bx = r.shape
+    d = np.empty_like(r)
+    m = _load().or_block_gmres(bx, by, bz, _dp(r), _dp(d), float(inner_rtol), int(inner_maxit), int(restart))
+    return d, r, int(m)
+
+
 def _cuts(c):
     return np.ascontiguousarray(c, dtype=np.int32)
 
 
 def solve(nx, ny, nz, cx, cy, cz, f=None, bnd=None, x0=None, inner_rtol=1e-6, inner_maxit=50,
-          outer_tol=1e-8, outer_maxit=100000, history=False, overlap=None):
+          outer_tol=1e-8, outer_maxit=100000, history=False, overlap=None, inner="cg", restart=10):
     """Block Jacobi with inner CG for ONE right-hand side.
 
     Returns a dict: x (nz, ny, nx), status, outer_its, inner_its, rel_residual,
     and history (relative residual of every iterate x^0..x^K) if requested.
     overlap: None = or_solve; o >= 0 = or_solve_overlap with blocks extended
     by o points per face (o = 0 gives or_solve's result).
+    inner: "cg" or "gmres" (restarted GMRES(restart), or_block_gmres).
     """
     cx, cy, cz = _cuts(cx), _cuts(cy), _cuts(cz)
     px, py, pz = len(cx) - 1, len(cy) - 1, len(cz) - 1
@@ -186,21 +201,28 @@ def solve(nx, ny, nz, cx, cy, cz, f=None, bnd=None, x0=None, inner_rtol=1e-6, in
     if bnd is not None and bnd.size != boundary_size(nx, ny, nz):
         raise ValueError("boundary array has the wrong size")
     outer = ctypes.c_int(0)
-    inner = ctypes.c_longlong(0)
+    inner_its_c = ctypes.c_longlong(0)
     rel = ctypes.c_double(0.0)
     hist = np.zeros(outer_maxit + 1) if history else None
-    if overlap is None:
+    if inner not in ("cg", "gmres"):
+        raise ValueError("inner must be 'cg' or 'gmres'")
+    if inner == "gmres":
+        st = _load().or_solve_ex(nx, ny, nz, px, py, pz, _ip(cx), _ip(cy), _ip(cz), int(overlap or 0), int(restart),
+                                 _dp(f), _dp(bnd), _dp(x), float(inner_rtol), int(inner_maxit), float(outer_tol),
+                                 int(outer_maxit), ctypes.byref(outer), ctypes.byref(inner_its_c), _dp(hist),
+                                 ctypes.byref(rel))
+    elif overlap is None:
         st = _load().or_solve(nx, ny, nz, px, py, pz, _ip(cx), _ip(cy), _ip(cz), _dp(f), _dp(bnd), _dp(x),
                               float(inner_rtol), int(inner_maxit), float(outer_tol), int(outer_maxit),
-                              ctypes.byref(outer), ctypes.byref(inner), _dp(hist), ctypes.byref(rel))
+                              ctypes.byref(outer), ctypes.byref(inner_its_c), _dp(hist), ctypes.byref(rel))
     else:
         st = _load().or_solve_overlap(nx, ny, nz, px, py, pz, _ip(cx), _ip(cy), _ip(cz), int(overlap), _dp(f),
                                       _dp(bnd), _dp(x), float(inner_rtol), int(inner_maxit), float(outer_tol),
-                                      int(outer_maxit), ctypes.byref(outer), ctypes.byref(inner), _dp(hist),
+                                      int(outer_maxit), ctypes.byref(outer), ctypes.byref(inner_its_c), _dp(hist),
                                       ctypes.byref(rel))
     if st == ERR_ARG:
         raise ValueError("oracle rejected the arguments")
-    out = dict(x=x, status=int(st), outer_its=int(outer.value), inner_its=int(inner.value),
+    out = dict(x=x, status=int(st), outer_its=int(outer.value), inner_its=int(inner_its_c.value),
                rel_residual=float(rel.value))
     if history:
         out["history"] = hist[: outer.value + 1].copy()

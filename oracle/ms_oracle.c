@@ -154,6 +154,104 @@ int or_block_cg(int bx, int by, int bz, double* r, double* d, double* work, doub
   return m;
 }
 
+/*
+ * Inner stage alternative: restarted GMRES(restart) on the block system
+ * A_ii d = r, from d = 0 -- the Krylov method of the paper's own runs
+ * (PETSc's GMRES, section 3.2), written from its textbook definition:
+ * Arnoldi with classical Gram-Schmidt (every projection of a step from the
+ * same vector w = A v_j, as in PETSc's default), Givens rotations on the
+ * Hessenberg column, |g_{j+1}| as the residual norm of the current iterate,
+ * d += V y at the end of a cycle, and the true residual r - A d recomputed
+ * at every restart.  Stops when the residual estimate is <= inner_rtol ||r||
+ * or after inner_maxit Arnoldi steps (the iteration count, one stencil
+ * application each, as for CG).  On return r holds the true residual
+ * r - A d.  Returns the number of Arnoldi steps.
+ */
+int or_block_gmres(int bx, int by, int bz, double* r, double* d, double inner_rtol, int inner_maxit, int restart) {
+  long long n = (long long)bx * by * bz;
+  if (restart < 1) restart = 1;
+  int m1 = restart + 1;
+  double* V = (double*)malloc(sizeof(double) * n * m1);  /* basis vectors, column j at V + j*n */
+  double* w = (double*)malloc(sizeof(double) * n);
+  double* H = (double*)calloc((size_t)m1 * restart, sizeof(double)); /* H[i*restart + j] */
+  double* cs = (double*)malloc(sizeof(double) * restart);
+  double* sn = (double*)malloc(sizeof(double) * restart);
+  double* g = (double*)malloc(sizeof(double) * m1);
+  double* y = (double*)malloc(sizeof(double) * restart);
+  for (long long t = 0; t < n; ++t) d[t] = 0.0;
+  double beta0 = sqrt(dot(n, r, r));
+  int total = 0;
+  if (beta0 > 0.0 && inner_maxit > 0) {
+    double stop = inner_rtol * beta0;
+    for (;;) {
+      /* residual of the current iterate: r - A d (r itself in the first cycle) */
+      or_apply_A(bx, by, bz, d, w);
+      for (long long t = 0; t < n; ++t) w[t] = r[t] - w[t];
+      double beta = sqrt(dot(n, w, w));
+      if (beta <= stop || beta == 0.0) break;
+      for (long long t = 0; t < n; ++t) V[t] = w[t] / beta;
+      for (int i = 0; i < m1; ++i) g[i] = 0.0;
+      g[0] = beta;
+      int k = 0;
+      int finished = 0;
+      for (int j = 0; j < restart; ++j) {
+        or_apply_A(bx, by, bz, V + (long long)j * n, w);
+        /* classical Gram-Schmidt: every h_ij from the same w */
+        for (int i = 0; i <= j; ++i) H[i * restart + j] = dot(n, w, V + (long long)i * n);
+        for (int i = 0; i <= j; ++i) {
+          double h = H[i * restart + j];
+          for (long long t = 0; t < n; ++t) w[t] -= h * V[(long long)i * n + t];
+        }
+        double hn = sqrt(dot(n, w, w));
+        H[(j + 1) * restart + j] = hn;
+        if (hn > 0.0)
+          for (long long t = 0; t < n; ++t) V[(long long)(j + 1) * n + t] = w[t] / hn;
+        /* earlier rotations on column j, then the rotation that zeroes H[j+1][j] */
+        for (int i = 0; i < j; ++i) {
+          double a = H[i * restart + j], b = H[(i + 1) * restart + j];
+          H[i * restart + j] = cs[i] * a + sn[i] * b;
+          H[(i + 1) * restart + j] = -sn[i] * a + cs[i] * b;
+        }
+        double a = H[j * restart + j], b = H[(j + 1) * restart + j];
+        double rho = sqrt(a * a + b * b);
+        cs[j] = rho > 0.0 ? a / rho : 1.0;
+        sn[j] = rho > 0.0 ? b / rho : 0.0;
+        H[j * restart + j] = rho;
+        H[(j + 1) * restart + j] = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+        total += 1;
+        k = j + 1;
+        if (fabs(g[j + 1]) <= stop || total >= inner_maxit || hn == 0.0) {
+          finished = 1;
+          break;
+        }
+      }
+      /* y = R^{-1} g (upper triangular k x k), d += V y */
+      for (int i = k - 1; i >= 0; --i) {
+        double s = g[i];
+        for (int c = i + 1; c < k; ++c) s -= H[i * restart + c] * y[c];
+        y[i] = H[i * restart + i] != 0.0 ? s / H[i * restart + i] : 0.0;
+      }
+      for (int i = 0; i < k; ++i)
+        for (long long t = 0; t < n; ++t) d[t] += y[i] * V[(long long)i * n + t];
+      if (finished && (fabs(g[k]) <= stop || total >= inner_maxit)) break;
+      if (total >= inner_maxit) break;
+    }
+  }
+  /* true residual of the final iterate */
+  or_apply_A(bx, by, bz, d, w);
+  for (long long t = 0; t < n; ++t) r[t] -= w[t];
+  free(V);
+  free(w);
+  free(H);
+  free(cs);
+  free(sn);
+  free(g);
+  free(y);
+  return total;
+}
+
 static int check_cuts(int n, int p, const int* c) {
   if (p < 1 || c[0] != 0 || c[p] != n) return 0;
   for (int a = 0; a < p; ++a)
@@ -279,7 +377,7 @@ int or_solve(int nx, int ny, int nz, int px, int py, int pz, const int* cx, cons
  */
 static long long overlap_sweep(int nx, int ny, int nz, int px, int py, int pz, const int* cx, const int* cy,
                                const int* cz, int o, const double* r_grid, double* x, double inner_rtol,
-                               int inner_maxit) {
+                               int inner_maxit, int gmres_restart) {
   int nblocks = px * py * pz;
   long long total = 0;
 #ifdef _OPENMP
@@ -297,7 +395,8 @@ static long long overlap_sweep(int nx, int ny, int nz, int px, int py, int pz, c
     double* db = (double*)malloc(sizeof(double) * n);
     double* wk = (double*)malloc(sizeof(double) * 2 * n);
     gather_block(nx, ny, r_grid, ex0, ey0, ez0, ex, ey, ez, rb);
-    int m = or_block_cg(ex, ey, ez, rb, db, wk, inner_rtol, inner_maxit);
+    int m = gmres_restart > 0 ? or_block_gmres(ex, ey, ez, rb, db, inner_rtol, inner_maxit, gmres_restart)
+                              : or_block_cg(ex, ey, ez, rb, db, wk, inner_rtol, inner_maxit);
     total += m;
     /* owned points only: the owned boxes are disjoint, and every x read this
        sweep went into r_grid before any update */
@@ -312,11 +411,12 @@ static long long overlap_sweep(int nx, int ny, int nz, int px, int py, int pz, c
   return total;
 }
 
-int or_solve_overlap(int nx, int ny, int nz, int px, int py, int pz, const int* cx, const int* cy, const int* cz,
-                     int overlap, const double* f, const double* bnd, double* x, double inner_rtol, int inner_maxit,
-                     double outer_tol, int outer_maxit, int* outer_its, long long* inner_its, double* res_hist,
-                     double* final_rel) {
-  if (nx < 1 || ny < 1 || nz < 1 || overlap < 0) return OR_ERR_ARG;
+/* Overlap o >= 0 and inner method (gmres_restart = 0: CG, > 0: GMRES(restart)). */
+int or_solve_ex(int nx, int ny, int nz, int px, int py, int pz, const int* cx, const int* cy, const int* cz,
+                int overlap, int gmres_restart, const double* f, const double* bnd, double* x, double inner_rtol,
+                int inner_maxit, double outer_tol, int outer_maxit, int* outer_its, long long* inner_its,
+                double* res_hist, double* final_rel) {
+  if (nx < 1 || ny < 1 || nz < 1 || overlap < 0 || gmres_restart < 0) return OR_ERR_ARG;
   if (!check_cuts(nx, px, cx) || !check_cuts(ny, py, cy) || !check_cuts(nz, pz, cz)) return OR_ERR_ARG;
   if (inner_maxit < 0 || outer_maxit < 0) return OR_ERR_ARG;
   long long n = (long long)nx * ny * nz;
@@ -343,7 +443,8 @@ int or_solve_overlap(int nx, int ny, int nz, int px, int py, int pz, const int* 
       break;
     }
     if (k == outer_maxit) break;
-    inner_total += overlap_sweep(nx, ny, nz, px, py, pz, cx, cy, cz, overlap, r, x, inner_rtol, inner_maxit);
+    inner_total +=
+        overlap_sweep(nx, ny, nz, px, py, pz, cx, cy, cz, overlap, r, x, inner_rtol, inner_maxit, gmres_restart);
     k += 1;
   }
   if (outer_its) *outer_its = k;
@@ -352,6 +453,14 @@ int or_solve_overlap(int nx, int ny, int nz, int px, int py, int pz, const int* 
   free(bhat);
   free(r);
   return status;
+}
+
+int or_solve_overlap(int nx, int ny, int nz, int px, int py, int pz, const int* cx, const int* cy, const int* cz,
+                     int overlap, const double* f, const double* bnd, double* x, double inner_rtol, int inner_maxit,
+                     double outer_tol, int outer_maxit, int* outer_its, long long* inner_its, double* res_hist,
+                     double* final_rel) {
+  return or_solve_ex(nx, ny, nz, px, py, pz, cx, cy, cz, overlap, 0, f, bnd, x, inner_rtol, inner_maxit, outer_tol,
+                     outer_maxit, outer_its, inner_its, res_hist, final_rel);
 }
 
 /*

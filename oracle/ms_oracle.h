@@ -24,6 +24,11 @@ int or_block_cg(int bx, int by, int bz, double* r, double* d, double* work, doub
 int or_solve(int nx, int ny, int nz, int px, int py, int pz, const int* cx, const int* cy, const int* cz,
              const double* f, const double* bnd, double* x, double inner_rtol, int inner_maxit, double outer_tol,
              int outer_maxit, int* outer_its, long long* inner_its, double* res_hist, double* final_rel);
+int or_block_gmres(int bx, int by, int bz, double* r, double* d, double inner_rtol, int inner_maxit, int restart);
+int or_solve_ex(int nx, int ny, int nz, int px, int py, int pz, const int* cx, const int* cy, const int* cz,
+                int overlap, int gmres_restart, const double* f, const double* bnd, double* x, double inner_rtol,
+                int inner_maxit, double outer_tol, int outer_maxit, int* outer_its, long long* inner_its,
+                double* res_hist, double* final_rel);
 int or_solve_overlap(int nx, int ny, int nz, int px, int py, int pz, const int* cx, const int* cy, const int* cz,
                      int overlap, const double* f, const double* bnd, double* x, double inner_rtol, int inner_maxit,
                      double outer_tol, int outer_maxit, int* outer_its, long long* inner_its, double* res_hist,

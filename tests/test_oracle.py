@@ -449,3 +449,79 @@ def test_small_overlap_needs_fewer_outer_sweeps(oracle_mod):
     g = rng(27).uniform(-1, 1, inputs.boundary_size(n, n, n))
     its = [oracle_mod.solve(n, n, n, c, c, c, bnd=g, outer_tol=1e-8, overlap=o)["outer_its"] for o in (0, 1, 2)]
     assert its[1] < its[0] and its[2] < its[1]
+
+
+# ---------------------------------------------------------------- GMRES inner solver
+def _block_matrix(bx, by, bz):
+    return kron_laplacian(bx, by, bz).toarray()
+
+
+@pytest.mark.parametrize("shape", [(4, 3, 3), (5, 4, 2), (3, 3, 3)])
+@pytest.mark.parametrize("steps", [1, 3, 6])
+def test_gmres_minimises_the_residual_over_the_krylov_space(oracle_mod, shape, steps):
+    """Without restart, j GMRES steps give the d in K_j(A, r) with the smallest
+    ||r - A d||: compared with a least-squares solve over an orthonormal basis
+    of the Krylov space built from powers of A (numpy, no oracle code)."""
+    bx, by, bz = shape
+    A = _block_matrix(bx, by, bz)
+    r0 = rng(30 + steps).standard_normal(bx * by * bz)
+    d, r_fin, m = oracle_mod.block_gmres(r0.reshape(bz, by, bx), 0.0, steps, steps)
+    assert m == steps
+    K = np.empty((r0.size, steps))
+    v = r0 / np.linalg.norm(r0)
+    for j in range(steps):
+        K[:, j] = v
+        v = A @ v
+        v /= np.linalg.norm(v)
+    Q, _ = np.linalg.qr(K)
+    y, *_ = np.linalg.lstsq(A @ Q, r0, rcond=None)
+    best = np.linalg.norm(r0 - A @ (Q @ y))
+    got = np.linalg.norm(r0 - A @ d.ravel())
+    assert got == pytest.approx(best, rel=1e-8, abs=1e-12)
+    # r is returned as the true residual of d
+    np.testing.assert_allclose(r_fin.ravel(), r0 - A @ d.ravel(), rtol=1e-12, atol=1e-12)
+
+
+def test_gmres_finite_termination_equals_lu(oracle_mod):
+    """With a restart at least the block size, GMRES is exact after <= n steps."""
+    bx, by, bz = 3, 4, 2
+    A = _block_matrix(bx, by, bz)
+    r0 = rng(35).standard_normal(bx * by * bz)
+    d, _, m = oracle_mod.block_gmres(r0.reshape(bz, by, bx), 1e-14, 100, 100)
+    assert m <= r0.size
+    np.testing.assert_allclose(d.ravel(), np.linalg.solve(A, r0), rtol=1e-9, atol=1e-11)
+
+
+def test_gmres_restarts_reduce_the_residual_monotonically(oracle_mod):
+    bx, by, bz = 8, 7, 6
+    A = _block_matrix(bx, by, bz)
+    r0 = rng(36).standard_normal(bx * by * bz)
+    norms = []
+    for maxit in (5, 10, 15, 20, 40):
+        d, _, m = oracle_mod.block_gmres(r0.reshape(bz, by, bx), 0.0, maxit, 5)
+        assert m == maxit
+        norms.append(np.linalg.norm(r0 - A @ d.ravel()))
+    assert all(b < a for a, b in zip(norms, norms[1:]))
+
+
+def test_gmres_inner_solves_converge_to_lu(oracle_mod):
+    nx, ny, nz = 8, 7, 6
+    r = rng(37)
+    g = r.standard_normal(inputs.boundary_size(nx, ny, nz))
+    A = kron_laplacian(nx, ny, nz).toarray()
+    x_lu = np.linalg.solve(A, bhat_independent(nx, ny, nz, None, g).ravel())
+    res = oracle_mod.solve(nx, ny, nz, [0, 4, 8], [0, 3, 7], [0, 3, 6], bnd=g, outer_tol=1e-12, inner="gmres",
+                           restart=10)
+    assert res["status"] == 0
+    assert np.linalg.norm(res["x"].ravel() - x_lu) <= np.linalg.cond(A) * 1e-12 * np.linalg.norm(x_lu)
+
+
+def test_gmres_exact_inner_solves_are_block_jacobi(oracle_mod):
+    """Inner GMRES to full accuracy is the same exact block Jacobi as inner CG."""
+    nx, ny, nz = 8, 6, 6
+    g = rng(38).standard_normal(inputs.boundary_size(nx, ny, nz))
+    cuts = ([0, 4, 8], [0, 3, 6], [0, 3, 6])
+    a = oracle_mod.solve(nx, ny, nz, *cuts, bnd=g, inner_rtol=1e-14, inner_maxit=500, outer_tol=0.0, outer_maxit=3)
+    b = oracle_mod.solve(nx, ny, nz, *cuts, bnd=g, inner_rtol=1e-14, inner_maxit=500, outer_tol=0.0, outer_maxit=3,
+                         inner="gmres", restart=60)
+    np.testing.assert_allclose(b["x"], a["x"], rtol=1e-10, atol=1e-11)
