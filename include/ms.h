@@ -113,6 +113,11 @@ typedef struct {
                             multisplitting with weight 1 on owned points, 0 on overlapped ones);
                             the global residual counts every point once.  Runs on the streaming
                             engine (engine 0 or 1). */
+  int inner_method;      /* sync mode: 0 (default) = CG; 1 = restarted GMRES(gmres_restart), the inner
+                            method of the paper's own runs (section 3.2), classical Gram-Schmidt
+                            Arnoldi; inner_rtol tests its residual estimate, inner_maxit caps its
+                            Arnoldi steps.  Runs on the scalar streaming engine (engine 0 or 1). */
+  int gmres_restart;     /* GMRES basis vectors per cycle, 1..16 (default 10) */
 } ms_opts;
 
 typedef struct {

@@ -87,7 +87,7 @@ def _stream_handle(device):
 def _make_opts(lib, mode="sync", precision="mixed", inner_rtol=1e-6, inner_maxit=50, outer_tol=1e-8,
                outer_maxit=100000, time_limit_ms=0.0, cluster=0, threads=0, slots=0, check_every=0, use_graph=True,
                slow_block=-1, slow_ns=0, profile=False, engine="auto", persistent="auto", variant=-1,
-               inner_adapt=False, overlap=0):
+               inner_adapt=False, overlap=0, inner="cg", gmres_restart=10):
     o = _lib.Opts()
     lib.ms_default_opts(ctypes.byref(o))
     o.mode = _lib.MODE[mode] if isinstance(mode, str) else int(mode)
@@ -111,6 +111,8 @@ def _make_opts(lib, mode="sync", precision="mixed", inner_rtol=1e-6, inner_maxit
     o.variant = int(variant)
     o.inner_adapt = 1 if inner_adapt else 0
     o.overlap = int(overlap)
+    o.inner_method = {"cg": 0, "gmres": 1}[inner] if isinstance(inner, str) else int(inner)
+    o.gmres_restart = int(gmres_restart)
     return o
 
 
@@ -200,7 +202,8 @@ class Grid:
         engine ('auto'|'streaming'|'resident'), persistent, variant (resident
         layout row, see resident_variants(); -1 = tuned), inner_adapt (sync:
         choose the inner tolerance at run time), overlap (sync: blocks extended
-        by this many points per face, streaming engine).
+        by this many points per face, streaming engine), inner ('cg'|'gmres'),
+        gmres_restart (GMRES basis size per cycle, 1..16).
         """
         return self._call(self._lib.ms_solve, f, bnd, x0, out, history, opts)
 

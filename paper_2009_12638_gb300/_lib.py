@@ -53,6 +53,8 @@ class Opts(ctypes.Structure):
         ("variant", ctypes.c_int),
         ("inner_adapt", ctypes.c_int),
         ("overlap", ctypes.c_int),
+        ("inner_method", ctypes.c_int),
+        ("gmres_restart", ctypes.c_int),
     ]
 
 

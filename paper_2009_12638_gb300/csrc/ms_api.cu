@@ -17,6 +17,7 @@
 
 #include "ms.h"
 #include "ms_internal.h"
+#include "ms_gmres.cuh"
 #include "ms_tune.h"
 
 using namespace ms;
@@ -155,6 +156,8 @@ extern "C" void ms_default_opts(ms_opts* o) {
   o->variant = -1;
   o->inner_adapt = 0;
   o->overlap = 0;
+  o->inner_method = 0;
+  o->gmres_restart = 10;
 }
 
 static std::vector<int> equal_cuts(int n, int p) {
@@ -273,6 +276,11 @@ static int check_opts(ms_grid* g, const ms_opts& o) {
     return fail(g, MS_ERR_ARG, "opts.variant must be -1 (tuned) or 0..%d", ms::res_variant_count() - 1);
   if (o.inner_adapt != 0 && o.inner_adapt != 1) return fail(g, MS_ERR_ARG, "opts.inner_adapt must be 0 or 1");
   if (o.overlap < 0) return fail(g, MS_ERR_ARG, "opts.overlap must be >= 0");
+  if (o.inner_method != 0 && o.inner_method != 1) return fail(g, MS_ERR_ARG, "opts.inner_method must be 0 (CG) or 1 (GMRES)");
+  if (o.inner_method == 1 && (o.gmres_restart < 1 || o.gmres_restart > kGmresMaxRestart))
+    return fail(g, MS_ERR_ARG, "opts.gmres_restart must be 1..%d", kGmresMaxRestart);
+  if (o.inner_method == 1 && (o.mode != MS_MODE_SYNC || o.engine == 2 || o.variant >= 0))
+    return fail(g, MS_ERR_ARG, "opts.inner_method GMRES runs in the synchronous mode on the streaming engine");
   if (o.overlap > 0 && o.mode != MS_MODE_SYNC)
     return fail(g, MS_ERR_ARG, "opts.overlap needs the synchronous mode (the asynchronous faces are one layer deep)");
   if (o.overlap > 0 && o.engine == 2)
@@ -617,14 +625,20 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
   // launch shape: an explicit request, a shape measured earlier for this
   // problem, or -- sync mode -- candidates measured on the first sweeps
   std::vector<LaunchShape> all;
-  // overlapping blocks run on the streaming engines (the resident layouts keep no owned range)
-  int rc = list_shapes(g->tuner, prec, o.mode, o.variant >= 0 ? 2 : (o.overlap > 0 ? 1 : o.engine), tasks, maxpts,
-                       o.cluster, o.threads,
-                       o.slots, o.variant, &all);
+  // overlapping blocks run on the streaming engines (the resident layouts keep
+  // no owned range); the GMRES inner solver on the scalar streaming engine only
+  const bool gmres = o.inner_method == 1;
+  const int eff_engine = o.variant >= 0 ? 2 : ((o.overlap > 0 || gmres) ? 1 : o.engine);
+  int rc = list_shapes(g->tuner, prec, o.mode, eff_engine, tasks, maxpts, o.cluster, o.threads, o.slots, o.variant,
+                       &all);
+  if (rc == 0 && gmres) {
+    all.erase(std::remove_if(all.begin(), all.end(), [](const LaunchShape& c) { return c.variant != -1; }), all.end());
+    if (all.empty()) rc = (int)cudaErrorInvalidConfiguration;
+  }
   if (rc != 0) return fail(g, MS_ERR_CUDA, "ms_solve: no launchable shape (%s)", cudaGetErrorString((cudaError_t)rc));
   LaunchShape shape = all.front();
   std::vector<LaunchShape> cands;
-  const std::vector<long long> sig = signature(prec, o.mode, o.engine, tasks);
+  const std::vector<long long> sig = signature(prec, o.mode, eff_engine + 10 * o.inner_method, tasks);
   {
     auto it = g->tuner.best.find(sig);
     const bool requested = o.cluster || o.threads || o.slots || o.variant >= 0;
@@ -657,7 +671,8 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
     int streaming_slots = shape.variant < 0 ? shape.slots : 0;  // scalar and vectorised streaming
     for (const LaunchShape& c : cands)
       if (c.variant < 0) streaming_slots = std::max(streaming_slots, c.slots);
-    if (streaming_slots > 0) MS_CUDA(g, g->scratch.reserve((size_t)streaming_slots * 4 * vec_stride * esz));
+    const int nvec = gmres ? o.gmres_restart + 3 : 4;  // CG: r, p0, p1, d; GMRES: r, d, m + 1 basis vectors
+    if (streaming_slots > 0) MS_CUDA(g, g->scratch.reserve((size_t)streaming_slots * nvec * vec_stride * esz));
   }
   MS_CUDA(g, g->tasks.reserve(tasks.size() * sizeof(Task)));
   MS_CUDA(g, g->partial.reserve((size_t)ntasks * sizeof(double)));
@@ -733,6 +748,8 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
     sa.inv_bnorm = invb;
     sa.err = &ctl->err;
     sa.inner_rtol_rhs = adapt ? rtol_rhs : nullptr;
+    sa.inner_method = o.inner_method;
+    sa.gmres_restart = o.gmres_restart;
     CheckArgs ca;
     ca.nrhs = g->nrhs;
     ca.ntasks = ntasks;

@@ -66,6 +66,8 @@ struct SweepArgs {
   const double* inv_bnorm;          // [nrhs] 1/||bhat|| (1 if bhat = 0): FP32 inner scaling
   int* err;
   const double* inner_rtol_rhs;  // [nrhs] per-rhs inner tolerance (opts.inner_adapt) or null: inner_rtol
+  int inner_method;              // 0 CG, 1 restarted GMRES (scalar streaming engine)
+  int gmres_restart;             // GMRES basis size per cycle (slot holds gmres_restart + 3 vectors)
 };
 
 __host__ __device__ inline double sweep_inner_rtol(const SweepArgs& a, int rhs) {

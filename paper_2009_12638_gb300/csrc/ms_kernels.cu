@@ -8,7 +8,8 @@
 //   1. forms the block residual r = bhat - A x^k in FP64 from x^k (the halo
 //      is read straight from the neighbours' part of x^k: every block reads
 //      the same x^k, strict Jacobi) and the block partial ||r_i||^2;
-//   2. runs the inner CG on A_ii d = r (ms_cg.cuh) in T = float or double;
+//   2. runs the inner CG on A_ii d = r (ms_cg.cuh) -- or restarted GMRES
+//      (ms_gmres.cuh) -- in T = float or double;
 //   3. writes x^{k+1}_i = x^k_i + d in FP64 into the other buffer.
 // x is double buffered, so the kernel boundary is the only grid-wide
 // synchronisation a sweep needs.  A one-CTA check kernel then sums the block
@@ -23,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include "ms_cg.cuh"
+#include "ms_gmres.cuh"
 #include "ms_device.cuh"
 #include "ms_internal.h"
 
@@ -31,6 +33,7 @@ namespace ms {
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT, 1) sweep_kernel(const SweepArgs a) {
   __shared__ RedSmem sm;
+  __shared__ GmresSmem gs;
   __shared__ int s_task[2];
   if (*a.all_done) return;
   const unsigned rank = cl_rank(), csize = cl_size(), slot = cl_id();
@@ -39,7 +42,11 @@ __global__ void __launch_bounds__(NT, 1) sweep_kernel(const SweepArgs a) {
   const double* __restrict__ xin = (k & 1) ? a.xbuf1 : a.xbuf0;
   double* __restrict__ xout = (k & 1) ? a.xbuf0 : a.xbuf1;
   const bool residual_only = (k >= a.outer_maxit);
+  const bool gmres = a.inner_method == 1;
   const CgVecs<T> v = slot_vecs<T>(a.scratch, a.vec_stride, slot);
+  const GmresVecs<T> gv = gmres_slot_vecs<T>(a.scratch, a.vec_stride, slot, a.gmres_restart);
+  T* const rvec = gmres ? gv.r : v.r;  // the slot layout differs between the two inner methods
+  T* const dvec = gmres ? gv.d : v.d;
   const Geo g = a.g;
   const long long nxy = (long long)g.nx * g.ny;
   int par = 0;
@@ -80,7 +87,7 @@ __global__ void __launch_bounds__(NT, 1) sweep_kernel(const SweepArgs a) {
           const double rr = bh - (6.0 * xr[gi] - si);
           if (owns(tk, c % tk.bx, c / tk.bx, z)) s_loc += rr * rr;  // the global norm counts owned points
           const T rt = (T)(rr * scale);
-          v.r[z * sl.plane + c] = rt;
+          rvec[z * sl.plane + c] = rt;
           g_loc += rt * rt;
         }
       }
@@ -95,8 +102,10 @@ __global__ void __launch_bounds__(NT, 1) sweep_kernel(const SweepArgs a) {
     red0[1] = sm.tot[1];
     if (rank == 0 && tid == 0) a.partial[t] = red0[0];
     if (residual_only) continue;
-    // ---- 2. inner CG
-    const int m = block_cg<T, NT>(v, sl, red0[1], sweep_inner_rtol(a, tk.rhs), a.inner_maxit, sm, rank, csize);
+    // ---- 2. inner solve
+    const int m = gmres ? block_gmres<T, NT>(gv, a.gmres_restart, sl, red0[1], sweep_inner_rtol(a, tk.rhs),
+                                             a.inner_maxit, sm, gs, rank, csize)
+                        : block_cg<T, NT>(v, sl, red0[1], sweep_inner_rtol(a, tk.rhs), a.inner_maxit, sm, rank, csize);
     // ---- 3. outer update into the other buffer (owned points only)
     double* __restrict__ xo = xout + rb;
     for (int c = tid; c < sl.plane; c += NT) {
@@ -104,7 +113,7 @@ __global__ void __launch_bounds__(NT, 1) sweep_kernel(const SweepArgs a) {
       for (int z = sl.z0; z < sl.z1; ++z) {
         if (!owns(tk, c % tk.bx, c / tk.bx, z)) continue;
         const long long gi = (long long)(tk.oz + z) * nxy + (long long)gy * g.nx + gx;
-        xo[gi] = (m > 0) ? xr[gi] + (double)v.d[z * sl.plane + c] * unscale : xr[gi];
+        xo[gi] = (m > 0) ? xr[gi] + (double)dvec[z * sl.plane + c] * unscale : xr[gi];
       }
     }
     if (rank == 0 && tid == 0 && m > 0) {

@@ -47,9 +47,9 @@ def test_ctypes_structs_match_c_layout(tmp_path):
 #include <stddef.h>
 #include "ms.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(ms_opts), offsetof(ms_opts, outer_tol), offsetof(ms_opts, res_hist),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(ms_opts), offsetof(ms_opts, outer_tol), offsetof(ms_opts, res_hist),
          offsetof(ms_opts, slow_ns), offsetof(ms_opts, time_limit_ms), offsetof(ms_opts, variant),
-         offsetof(ms_opts, inner_adapt), offsetof(ms_opts, overlap));
+         offsetof(ms_opts, inner_adapt), offsetof(ms_opts, overlap), offsetof(ms_opts, gmres_restart));
   printf("%zu %zu %zu %zu %zu %zu\n", sizeof(ms_stats), offsetof(ms_stats, lups), offsetof(ms_stats, per_rhs_rel),
          offsetof(ms_stats, slots), offsetof(ms_stats, variant), offsetof(ms_stats, inner_rtol_final));
   return 0;
@@ -61,7 +61,7 @@ int main(void) {
     O, S = _lib.Opts, _lib.Stats
     assert [int(v) for v in a.split()] == [ctypes.sizeof(O), O.outer_tol.offset, O.res_hist.offset,
                                           O.slow_ns.offset, O.time_limit_ms.offset, O.variant.offset,
-                                          O.inner_adapt.offset, O.overlap.offset]
+                                          O.inner_adapt.offset, O.overlap.offset, O.gmres_restart.offset]
     assert [int(v) for v in b.split()] == [ctypes.sizeof(S), S.lups.offset, S.per_rhs_rel.offset, S.slots.offset,
                                           S.variant.offset, S.inner_rtol_final.offset]
 
@@ -71,7 +71,8 @@ def test_default_opts(lib):
     lib.ms_default_opts(ctypes.byref(o))
     assert (o.mode, o.precision, o.inner_rtol, o.inner_maxit, o.outer_tol) == (0, 1, 1e-6, 50, 1e-8)
     assert o.slow_block == -1 and o.use_graph == 1
-    assert o.variant == -1 and o.inner_adapt == 0
+    assert o.variant == -1 and o.inner_adapt == 0 and o.overlap == 0
+    assert o.inner_method == 0 and o.gmres_restart == 10
 
 
 def test_resident_variant_table(lib):
@@ -144,7 +145,7 @@ def test_solve_rejects_bad_arguments_before_device_work(lib):
         dummy = ctypes.c_void_p(16)  # never dereferenced: options are checked first
         for field, value in [("mode", 7), ("precision", 3), ("inner_maxit", -1), ("threads", 100),
                              ("cluster", 17), ("outer_tol", -1.0), ("time_limit_ms", -5.0), ("variant", -2),
-                             ("variant", 10000), ("inner_adapt", 2), ("overlap", -1)]:
+                             ("variant", 10000), ("inner_adapt", 2), ("overlap", -1), ("inner_method", 2)]:
             o2 = _lib.Opts()
             lib.ms_default_opts(ctypes.byref(o2))
             setattr(o2, field, value)
@@ -154,6 +155,14 @@ def test_solve_rejects_bad_arguments_before_device_work(lib):
         lib.ms_default_opts(ctypes.byref(o2))
         o2.inner_adapt, o2.mode = 1, 1
         assert lib.ms_solve(h, None, None, dummy, ctypes.byref(o2), None, None) == _lib.MS_ERR_ARG
+        # GMRES: restart range, sync mode, streaming engine
+        for fields in [dict(inner_method=1, gmres_restart=0), dict(inner_method=1, gmres_restart=17),
+                       dict(inner_method=1, mode=1), dict(inner_method=1, engine=2)]:
+            o2 = _lib.Opts()
+            lib.ms_default_opts(ctypes.byref(o2))
+            for k2, v2 in fields.items():
+                setattr(o2, k2, v2)
+            assert lib.ms_solve(h, None, None, dummy, ctypes.byref(o2), None, None) == _lib.MS_ERR_ARG, fields
         # overlapping blocks: sync mode and the streaming engine only
         for mode, eng in [(1, 0), (0, 2)]:
             o2 = _lib.Opts()
