@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 METRIC = "time-to-rel-residual-1e-8 and stencil GLUP/s vs plain FP64 sync; HBM GB/s vs peak"
 UNIT = "GLUP/s"
 WORKLOAD = "laplace256_u11"
-# algorithmic bytes per lattice update (roofline): the inner CG must
+# algorithmic bytes per lattice update (the roofline's numerator): the inner CG must
 # read and write r, p and d once per iteration (24 B at FP32, 48 B at FP64);
 # an outer sweep reads x (8 B) and writes r (4 B), then reads x and d and
 # writes x (20 B): 32 B per point at FP32 (the FP64 r/d add 8 B).
@@ -78,6 +78,7 @@ def parse():
     ap.add_argument("--overlap", type=int, default=0, help="overlapping blocks: points per face (sync mode)")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64-sync and async comparison solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--clock-log", default=None, help="directory for the raw nvidia-smi clock samples (CSV)")
     ap.add_argument("--sweeps", type=int, default=0,
                     help="profiling aid: run exactly this many outer sweeps once (no warm-up, no timing) and exit")
     return ap.parse_args()
@@ -89,10 +90,15 @@ class ClockSampler:
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, log_dir=None):
+        """Samples nvidia-smi every 200 ms into a CSV (in log_dir if given, else a temporary file)."""
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        if log_dir:
+            self.path = os.path.join(log_dir, f"clocks_rank{index}.csv")
+        else:
+            import tempfile
+            self.path = os.path.join(tempfile.gettempdir(), f"ms_bench_clocks_{os.getpid()}_{index}.csv")
 
     def start(self):
         try:
@@ -243,7 +249,7 @@ def main():
     for _ in range(max(args.warmup, 3)):
         _, st = solve_once()
         assert st.status == 0, st
-    sampler = ClockSampler(local)
+    sampler = ClockSampler(local, args.clock_log)
     sampler.start()
     if world > 1:
         dist.barrier()
