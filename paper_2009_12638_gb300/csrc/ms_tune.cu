@@ -70,7 +70,12 @@ static void list_resident(Tuner& t, int mode, const std::vector<Task>& tasks, lo
       r.smem = (size_t)smem;
       // rounds of the task queue x points each CTA handles per round
       const double rounds = std::ceil((double)ntasks / r.slots);
-      r.est = rounds * ((double)maxpts / c) * (1.0 + 0.02 * c) * (qr ? 0.85 : 1.0);  // QR: one stencil per iteration
+      // QR: one stencil per iteration.  The asynchronous kernel (never timed by
+      // the tuner) holds more state: with q in registers it spills at 512 and
+      // 1024 threads (measured 5% slower at 256^3), so there QR only pays at
+      // <= 256 threads (measured 27% faster at 128^3)
+      const double qr_factor = !qr ? 1.0 : (mode == 1 && nt > 256 ? 1.05 : 0.85);
+      r.est = rounds * ((double)maxpts / c) * (1.0 + 0.02 * c) * qr_factor;
       out->push_back(r);
     }
   }
