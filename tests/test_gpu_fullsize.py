@@ -116,3 +116,26 @@ def test_adjoint128_central_fd():
         fd = (L(eps) - L(-eps)) / (2 * eps)
         ad = float((f.grad * v_f).sum() + (gb.grad * v_g).sum())
         assert abs(ad - fd) <= 1e-6 * abs(fd), (i, ad, fd)
+
+
+def test_laplace256_overlap5_and_adaptive_converge():
+    """The bench's comparison paths at full size: overlapping blocks (5 points
+    per face) and the inner-tolerance controller reach the true residual."""
+    cfg = inputs.make_config("laplace256_u11")
+    g = grid_for(cfg)
+    b = torch.from_numpy(cfg["bnd"]).cuda()
+    for opts in (dict(overlap=5), dict(inner_adapt=True)):
+        x, st = g.solve(bnd=b, precision="mixed", **opts)
+        assert st.status == 0 and st.rel_residual < 1e-8, opts
+        assert g.residual(x, bnd=b)[0] < 1e-8, opts
+
+
+def test_laplace256_gmres_first_sweep_fp64():
+    cfg = inputs.make_config("laplace256_u11")
+    g = grid_for(cfg)
+    x, st = g.solve(bnd=torch.from_numpy(cfg["bnd"]).cuda(), precision="fp64", inner="gmres", outer_tol=0.0,
+                    outer_maxit=1)
+    ref = oracle.solve(cfg["nx"], cfg["ny"], cfg["nz"], cfg["cx"], cfg["cy"], cfg["cz"], bnd=cfg["bnd"][0],
+                       outer_tol=0.0, outer_maxit=1, inner="gmres", restart=10)
+    assert rel_inf(x.cpu().numpy()[0], ref["x"]) <= 1e-10
+    assert st.inner_its == ref["inner_its"]
