@@ -100,6 +100,47 @@ __device__ __forceinline__ void cluster_reduce(const TA (&v)[NV], double (*slots
   __syncthreads();
 }
 
+__device__ __forceinline__ void st_cluster_f32(float* local, unsigned rank, float v) {
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(cl_map(local, rank)), "f"(v) : "memory");
+}
+
+// Cluster-wide FP32 sum.  Warp totals (xor butterfly: every lane holds the
+// same bits) go to `wsum`; after one CTA barrier warp 0 adds them and stores
+// the CTA total into slot[rank] of every CTA; after the cluster barrier
+// EVERY warp adds the csize slots in the same order, so every thread of the
+// cluster holds the bit-identical total.  Pre-reducing inside the CTA keeps
+// the remote stores per sum at csize per CTA (instead of one per warp and
+// CTA), which shortens the cluster barrier's release.  `slots` and `wsum`
+// must not be reused by another sum before the next cluster barrier.
+template <int NT>
+__device__ __forceinline__ float cluster_sum_f32(float v, float* slots, float* wsum, unsigned rank, unsigned csize) {
+  constexpr int NW = NT / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) wsum[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    float t = lane < NW ? wsum[lane] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane < (int)csize) st_cluster_f32(&slots[rank], (unsigned)lane, t);
+  }
+  cl_barrier();
+  float acc = lane < (int)csize ? slots[lane] : 0.f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  return acc;
+}
+
+// Reduction slots of an FP32 CG iteration (resident and vectorised streaming
+// engines): CTA totals, one per rank, and this CTA's warp totals, for the
+// iteration's two sums (see cluster_sum_f32).
+struct ResRed {
+  float eta[kMaxCluster], gam[kMaxCluster];
+  float weta[32], wgam[32];
+};
+
 // Shared memory used by the reductions of one cluster, and the CG scalars
 // that thread 0 derives from them and every thread reads.
 struct RedSmem {

@@ -67,39 +67,6 @@ __device__ __forceinline__ float4 mask4(float4 v, unsigned m) {
 
 __device__ __forceinline__ float dot4(float4 a, float4 b) { return (a.x * b.x + a.y * b.y) + (a.z * b.z + a.w * b.w); }
 
-__device__ __forceinline__ void st_cluster_f32(float* local, unsigned rank, float v) {
-  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(cl_map(local, rank)), "f"(v) : "memory");
-}
-
-// Cluster-wide FP32 sum.  Warp totals (xor butterfly: every lane holds the
-// same bits) go to `wsum`; after one CTA barrier warp 0 adds them and stores
-// the CTA total into slot[rank] of every CTA; after the cluster barrier
-// EVERY warp adds the csize slots in the same order, so every thread of the
-// cluster holds the bit-identical total.  Pre-reducing inside the CTA keeps
-// the remote stores per sum at csize per CTA (instead of one per warp and
-// CTA), which shortens the cluster barrier's release.  `slots` and `wsum`
-// must not be reused by another sum before the next cluster barrier.
-template <int NT>
-__device__ __forceinline__ float cluster_sum_f32(float v, float* slots, float* wsum, unsigned rank, unsigned csize) {
-  constexpr int NW = NT / 32;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if (lane == 0) wsum[warp] = v;
-  __syncthreads();
-  if (warp == 0) {
-    float t = lane < NW ? wsum[lane] : 0.f;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane < (int)csize) st_cluster_f32(&slots[rank], (unsigned)lane, t);
-  }
-  cl_barrier();
-  float acc = lane < (int)csize ? slots[lane] : 0.f;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  return acc;
-}
-
 // 7-point stencil q = 6p - sum(nbrs) on the 4 points of a strip.  y and z
 // neighbours come from shared memory / registers; the x neighbours at the
 // strip ends come from the adjacent lanes (which hold the adjacent strips of
@@ -155,13 +122,6 @@ __device__ __forceinline__ Strips<KC> make_strips(const ResGeo& g) {
   }
   return s;
 }
-
-// Reduction slots of the resident engine (FP32): CTA totals, one per rank,
-// and this CTA's warp totals, for the two sums of a CG iteration.
-struct ResRed {
-  float eta[kMaxCluster], gam[kMaxCluster];
-  float weta[32], wgam[32];
-};
 
 // Inner CG on the resident state.  On entry r4 holds r (padding lanes 0),
 // the r-halo planes hold the neighbours' boundary r (pushed before the

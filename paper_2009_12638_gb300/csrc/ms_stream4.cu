@@ -91,19 +91,22 @@ __device__ __forceinline__ float4 stencil_strip(float4 c, float4 zm, float4 zp, 
 // The inner CG on the strip layout.  Vectors r, p0, p1, d of the slot use the
 // pitch-padded layout (z, y, 4*xs + lane); r holds the residual on entry
 // (padding lanes zero), gamma0 = r.r reduced.  Returns m; d holds the
-// correction when m > 0.
+// correction when m > 0.  The two sums of an iteration are FP32 cluster sums
+// pre-reduced inside each CTA (cluster_sum_f32), and every thread forms the
+// same FP32 scalars alpha, beta and the stop test from them (no broadcast).
 template <int NT>
-__device__ int strip_cg(const CgVecs<float>& v, const StripGeo& g, double gamma0, double inner_rtol, int inner_maxit,
-                        RedSmem& sm, unsigned rank, unsigned csize) {
-  cg_begin(sm, gamma0, inner_rtol, inner_maxit);
-  if (sm.done) return 0;
+__device__ int strip_cg(const CgVecs<float>& v, const StripGeo& g, float gamma0, float inner_rtol, int inner_maxit,
+                        ResRed& rr, unsigned rank, unsigned csize) {
+  if (!(gamma0 > 0.f) || inner_maxit <= 0) return 0;
   const int lane = threadIdx.x & 31;
   const int wbase = threadIdx.x - lane;
+  const float stop = inner_rtol * sqrtf(gamma0);
+  float gamma = gamma0, beta = 0.f;
+  int m = 0;
   float* po = v.p0;
   float* pn = v.p1;
   bool first = true;
   for (;;) {
-    const float beta = sm.beta;
     // ---------------- pass A: p_new at the strip and its neighbours, q = A_ii p_new, eta = p.q
     // (within a pass the vectors are distinct: pass A reads r and p_old and writes
     // p_new, so the next planes' loads may move ahead of this plane's store)
@@ -136,12 +139,9 @@ __device__ int strip_cg(const CgVecs<float>& v, const StripGeo& g, double gamma0
         c = zp;
       }
     }
-    {
-      const float red1[1] = {eta_loc};
-      cluster_reduce<NT, 1>(red1, sm.slots[1], sm.wsum, rank, csize, [&](double (&t)[1]) { cg_after_eta(sm, t[0]); });
-    }
-    if (sm.done) break;
-    const float alpha = sm.alpha;
+    const float eta = cluster_sum_f32<NT>(eta_loc, rr.eta, rr.weta, rank, csize);
+    if (!(eta > 0.f)) break;  // curvature breakdown or NaN: keep d from earlier steps
+    const float alpha = gamma / eta;
     // ---------------- pass B: q = A_ii p_new again, d += alpha p, r -= alpha q, gamma = r.r
     // (reads p_new; d and r are read and written at the strip itself only)
     const float* __restrict__ pnB = pn;
@@ -174,18 +174,17 @@ __device__ int strip_cg(const CgVecs<float>& v, const StripGeo& g, double gamma0
         c = zp;
       }
     }
-    {
-      const float red2[1] = {g_loc};
-      cluster_reduce<NT, 1>(red2, sm.slots[2], sm.wsum, rank, csize,
-                            [&](double (&t)[1]) { cg_after_gamma(sm, t[0], inner_maxit); });
-    }
-    if (sm.done) break;
+    const float gnew = cluster_sum_f32<NT>(g_loc, rr.gam, rr.wgam, rank, csize);
+    m += 1;
+    if (sqrtf(gnew) <= stop || m >= inner_maxit) break;
+    beta = gnew / gamma;
+    gamma = gnew;
     first = false;
     float* tp = po;
     po = pn;
     pn = tp;
   }
-  return sm.m;
+  return m;
 }
 
 // One synchronous outer sweep with the vectorised streaming CG (contract of
@@ -193,6 +192,7 @@ __device__ int strip_cg(const CgVecs<float>& v, const StripGeo& g, double gamma0
 template <int NT>
 __global__ void __launch_bounds__(NT, 1) strip_sweep_kernel(const SweepArgs a) {
   __shared__ RedSmem sm;
+  __shared__ ResRed rred;
   __shared__ int s_task[2];
   if (*a.all_done) return;
   const unsigned rank = cl_rank(), csize = cl_size(), slot = cl_id();
@@ -266,7 +266,8 @@ __global__ void __launch_bounds__(NT, 1) strip_sweep_kernel(const SweepArgs a) {
     if (rank == 0 && tid == 0) a.partial[t] = sm.tot[0];
     if (residual_only) continue;
     // ---- 2. inner CG
-    const int m = strip_cg<NT>(v, g, sm.tot[1], sweep_inner_rtol(a, tk.rhs), a.inner_maxit, sm, rank, csize);
+    const int m = strip_cg<NT>(v, g, (float)sm.tot[1], (float)sweep_inner_rtol(a, tk.rhs), a.inner_maxit, rred, rank,
+                               csize);
     // ---- 3. outer update into the other buffer (owned points only)
     double* __restrict__ xo = xout + rb;
     for (int s0 = wbase; s0 < g.nstrips; s0 += NT) {
