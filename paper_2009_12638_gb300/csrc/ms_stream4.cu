@@ -88,6 +88,8 @@ __device__ __forceinline__ float4 stencil_strip(float4 c, float4 zm, float4 zp, 
 
 }  // namespace
 
+constexpr int kStripsInFlight = 2;  // strip columns a thread marches up z together
+
 // The inner CG on the strip layout.  Vectors r, p0, p1, d of the slot use the
 // pitch-padded layout (z, y, 4*xs + lane); r holds the residual on entry
 // (padding lanes zero), gamma0 = r.r reduced.  Returns m; d holds the
@@ -109,34 +111,48 @@ __device__ int strip_cg(const CgVecs<float>& v, const StripGeo& g, float gamma0,
   for (;;) {
     // ---------------- pass A: p_new at the strip and its neighbours, q = A_ii p_new, eta = p.q
     // (within a pass the vectors are distinct: pass A reads r and p_old and writes
-    // p_new, so the next planes' loads may move ahead of this plane's store)
+    // p_new, so the next planes' loads may move ahead of this plane's store).
+    // Each thread marches kStripsInFlight strip columns up z together, so twice
+    // as many independent loads are in flight per plane step.
     const float* __restrict__ rA = v.r;
     const float* __restrict__ poA = po;
     float* __restrict__ pnA = pn;
+    auto pnew = [&](long long i) -> float4 {  // i: float index of a strip start
+      const float4 r = ld4(rA + i);
+      return first ? r : fma4(beta, ld4(poA + i), r);
+    };
+    auto pnew_s = [&](long long i) -> float { return first ? rA[i] : fmaf(beta, poA[i], rA[i]); };
     float eta_loc = 0.f;
-    for (int s0 = wbase; s0 < g.nstrips; s0 += NT) {
-      const StripPos s = strip_pos(g, s0 + lane, lane);
-      auto pnew = [&](long long i) -> float4 {  // i: float index of a strip start
-        const float4 r = ld4(rA + i);
-        return first ? r : fma4(beta, ld4(poA + i), r);
-      };
-      auto pnew_s = [&](long long i) -> float { return first ? rA[i] : fmaf(beta, poA[i], rA[i]); };
-      float4 zm = (s.has && g.z0 > 0 && g.z0 < g.z1) ? pnew((long long)(g.z0 - 1) * g.plane + s.off) : zero4();
-      float4 c = (s.has && g.z0 < g.z1) ? pnew((long long)g.z0 * g.plane + s.off) : zero4();
+    for (int s0 = wbase; s0 < g.nstrips; s0 += kStripsInFlight * NT) {
+      StripPos s[kStripsInFlight];
+      float4 zm[kStripsInFlight], c[kStripsInFlight];
+#pragma unroll
+      for (int u = 0; u < kStripsInFlight; ++u) {
+        s[u] = strip_pos(g, s0 + u * NT + lane, lane);
+        zm[u] = (s[u].has && g.z0 > 0 && g.z0 < g.z1) ? pnew((long long)(g.z0 - 1) * g.plane + s[u].off) : zero4();
+        c[u] = (s[u].has && g.z0 < g.z1) ? pnew((long long)g.z0 * g.plane + s[u].off) : zero4();
+      }
       for (int z = g.z0; z < g.z1; ++z) {
         const long long base = (long long)z * g.plane;
-        const float4 zp = (s.has && z + 1 < g.bz) ? pnew(base + g.plane + s.off) : zero4();
-        const float4 ym = (s.has && s.y > 0) ? pnew(base + s.off - g.pitch) : zero4();
-        const float4 yp = (s.has && s.y + 1 < g.by) ? pnew(base + s.off + g.pitch) : zero4();
-        const float l_sh = __shfl_up_sync(0xffffffffu, c.w, 1);
-        const float r_sh = __shfl_down_sync(0xffffffffu, c.x, 1);
-        const float xl = s.lin ? l_sh : ((s.has && s.xs > 0) ? pnew_s(base + s.off - 1) : 0.f);
-        const float xr = s.rin ? r_sh : ((s.has && s.xs + 1 < g.spr) ? pnew_s(base + s.off + 4) : 0.f);
-        const float4 q = msk4(stencil_strip(c, zm, zp, ym, yp, xl, xr), s.msk);
-        if (s.has) st4(pnA + base + s.off, c);
-        eta_loc += dot4f(c, q);
-        zm = c;
-        c = zp;
+        float4 zp[kStripsInFlight], ym[kStripsInFlight], yp[kStripsInFlight];
+#pragma unroll
+        for (int u = 0; u < kStripsInFlight; ++u) {
+          zp[u] = (s[u].has && z + 1 < g.bz) ? pnew(base + g.plane + s[u].off) : zero4();
+          ym[u] = (s[u].has && s[u].y > 0) ? pnew(base + s[u].off - g.pitch) : zero4();
+          yp[u] = (s[u].has && s[u].y + 1 < g.by) ? pnew(base + s[u].off + g.pitch) : zero4();
+        }
+#pragma unroll
+        for (int u = 0; u < kStripsInFlight; ++u) {
+          const float l_sh = __shfl_up_sync(0xffffffffu, c[u].w, 1);
+          const float r_sh = __shfl_down_sync(0xffffffffu, c[u].x, 1);
+          const float xl = s[u].lin ? l_sh : ((s[u].has && s[u].xs > 0) ? pnew_s(base + s[u].off - 1) : 0.f);
+          const float xr = s[u].rin ? r_sh : ((s[u].has && s[u].xs + 1 < g.spr) ? pnew_s(base + s[u].off + 4) : 0.f);
+          const float4 q = msk4(stencil_strip(c[u], zm[u], zp[u], ym[u], yp[u], xl, xr), s[u].msk);
+          if (s[u].has) st4(pnA + base + s[u].off, c[u]);
+          eta_loc += dot4f(c[u], q);
+          zm[u] = c[u];
+          c[u] = zp[u];
+        }
       }
     }
     const float eta = cluster_sum_f32<NT>(eta_loc, rr.eta, rr.weta, rank, csize);
@@ -148,30 +164,45 @@ __device__ int strip_cg(const CgVecs<float>& v, const StripGeo& g, float gamma0,
     float* __restrict__ dB = v.d;
     float* __restrict__ rB = v.r;
     float g_loc = 0.f;
-    for (int s0 = wbase; s0 < g.nstrips; s0 += NT) {
-      const StripPos s = strip_pos(g, s0 + lane, lane);
-      float4 zm = (s.has && g.z0 > 0 && g.z0 < g.z1) ? ld4(pnB + (long long)(g.z0 - 1) * g.plane + s.off) : zero4();
-      float4 c = (s.has && g.z0 < g.z1) ? ld4(pnB + (long long)g.z0 * g.plane + s.off) : zero4();
+    for (int s0 = wbase; s0 < g.nstrips; s0 += kStripsInFlight * NT) {
+      StripPos s[kStripsInFlight];
+      float4 zm[kStripsInFlight], c[kStripsInFlight];
+#pragma unroll
+      for (int u = 0; u < kStripsInFlight; ++u) {
+        s[u] = strip_pos(g, s0 + u * NT + lane, lane);
+        zm[u] = (s[u].has && g.z0 > 0 && g.z0 < g.z1) ? ld4(pnB + (long long)(g.z0 - 1) * g.plane + s[u].off) : zero4();
+        c[u] = (s[u].has && g.z0 < g.z1) ? ld4(pnB + (long long)g.z0 * g.plane + s[u].off) : zero4();
+      }
       for (int z = g.z0; z < g.z1; ++z) {
         const long long base = (long long)z * g.plane;
-        const float4 zp = (s.has && z + 1 < g.bz) ? ld4(pnB + base + g.plane + s.off) : zero4();
-        const float4 ym = (s.has && s.y > 0) ? ld4(pnB + base + s.off - g.pitch) : zero4();
-        const float4 yp = (s.has && s.y + 1 < g.by) ? ld4(pnB + base + s.off + g.pitch) : zero4();
-        const float l_sh = __shfl_up_sync(0xffffffffu, c.w, 1);
-        const float r_sh = __shfl_down_sync(0xffffffffu, c.x, 1);
-        const float xl = s.lin ? l_sh : ((s.has && s.xs > 0) ? pnB[base + s.off - 1] : 0.f);
-        const float xr = s.rin ? r_sh : ((s.has && s.xs + 1 < g.spr) ? pnB[base + s.off + 4] : 0.f);
-        const float4 q = msk4(stencil_strip(c, zm, zp, ym, yp, xl, xr), s.msk);
-        if (s.has) {
-          const long long i = base + s.off;
-          const float4 d = first ? zero4() : ld4(dB + i);
-          st4(dB + i, fma4(alpha, c, d));
-          const float4 r = fma4(-alpha, q, ld4(rB + i));
-          st4(rB + i, r);
-          g_loc += dot4f(r, r);
+        float4 zp[kStripsInFlight], ym[kStripsInFlight], yp[kStripsInFlight], dd[kStripsInFlight],
+            ro[kStripsInFlight];
+#pragma unroll
+        for (int u = 0; u < kStripsInFlight; ++u) {
+          const long long i = base + s[u].off;
+          zp[u] = (s[u].has && z + 1 < g.bz) ? ld4(pnB + i + g.plane) : zero4();
+          ym[u] = (s[u].has && s[u].y > 0) ? ld4(pnB + i - g.pitch) : zero4();
+          yp[u] = (s[u].has && s[u].y + 1 < g.by) ? ld4(pnB + i + g.pitch) : zero4();
+          dd[u] = (s[u].has && !first) ? ld4(dB + i) : zero4();
+          ro[u] = s[u].has ? ld4(rB + i) : zero4();
         }
-        zm = c;
-        c = zp;
+#pragma unroll
+        for (int u = 0; u < kStripsInFlight; ++u) {
+          const long long i = base + s[u].off;
+          const float l_sh = __shfl_up_sync(0xffffffffu, c[u].w, 1);
+          const float r_sh = __shfl_down_sync(0xffffffffu, c[u].x, 1);
+          const float xl = s[u].lin ? l_sh : ((s[u].has && s[u].xs > 0) ? pnB[i - 1] : 0.f);
+          const float xr = s[u].rin ? r_sh : ((s[u].has && s[u].xs + 1 < g.spr) ? pnB[i + 4] : 0.f);
+          const float4 q = msk4(stencil_strip(c[u], zm[u], zp[u], ym[u], yp[u], xl, xr), s[u].msk);
+          if (s[u].has) {
+            st4(dB + i, fma4(alpha, c[u], dd[u]));
+            const float4 r = fma4(-alpha, q, ro[u]);
+            st4(rB + i, r);
+            g_loc += dot4f(r, r);
+          }
+          zm[u] = c[u];
+          c[u] = zp[u];
+        }
       }
     }
     const float gnew = cluster_sum_f32<NT>(g_loc, rr.gam, rr.wgam, rank, csize);
