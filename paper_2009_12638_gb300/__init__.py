@@ -69,6 +69,7 @@ class SolveStats:
     engine: int = 0
     variant: int = -1
     inner_rtol_final: float = 0.0
+    history_ms: np.ndarray | None = None
     history: np.ndarray | None = None
 
     @property
@@ -227,10 +228,12 @@ class Grid:
             if x0 is not None and x0.data_ptr() != out.data_ptr():
                 out.copy_(self._field(x0, "x0", self.shape, allow_none=False))
         o = _make_opts(self._lib, **opts)
-        hist = None
+        hist = thist = None
         if history:
             hist = np.zeros((self.nrhs, o.outer_maxit + 1))
             o.res_hist = hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            thist = np.zeros(o.outer_maxit + 1)
+            o.time_hist = thist.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         st = _lib.Stats()
         per_its = (ctypes.c_int * self.nrhs)()
         per_rel = (ctypes.c_double * self.nrhs)()
@@ -246,6 +249,7 @@ class Grid:
                            st.sweep_launches, st.engine, st.variant, st.inner_rtol_final)
         if hist is not None:
             stats.history = hist
+            stats.history_ms = thist
         return out, stats
 
     def solve_host(self, f=None, bnd=None, x=None, **opts):

@@ -55,6 +55,7 @@ class Opts(ctypes.Structure):
         ("overlap", ctypes.c_int),
         ("inner_method", ctypes.c_int),
         ("gmres_restart", ctypes.c_int),
+        ("time_hist", ctypes.POINTER(ctypes.c_double)),
     ]
 
 

@@ -87,6 +87,7 @@ struct ms_grid {
   DevBuf async_ws; // face buffers, halos, seq counters (async mode)
   DevBuf flow_ws;  // tickets, per-task progress, per-sweep counters (persistent sync mode)
   DevBuf gcg_ws;   // global CG: r, p, q, partial sums, control words
+  DevBuf thist;    // [outer_maxit+1] stop-test times (opts.time_hist)
   Tuner tuner;
   long long npts() const { return (long long)nx * ny * nz; }
   long long nbnd() const { return ms_boundary_size(nx, ny, nz); }
@@ -158,6 +159,7 @@ extern "C" void ms_default_opts(ms_opts* o) {
   o->overlap = 0;
   o->inner_method = 0;
   o->gmres_restart = 10;
+  o->time_hist = nullptr;
 }
 
 static std::vector<int> equal_cuts(int n, int p) {
@@ -586,6 +588,7 @@ extern "C" int ms_destroy(ms_grid* g) {
   g->async_ws.release();
   g->flow_ws.release();
   g->gcg_ws.release();
+  g->thist.release();
   g->tuner.release();
   delete g;
   return MS_OK;
@@ -726,6 +729,12 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
       MS_CUDA(g, g->hist.reserve((size_t)g->nrhs * (o.outer_maxit + 1) * sizeof(double)));
       hist_dev = g->hist.as<double>();
     }
+    double* thist_dev = nullptr;
+    if (o.time_hist) {
+      MS_CUDA(g, g->thist.reserve((size_t)(o.outer_maxit + 1) * sizeof(double)));
+      thist_dev = g->thist.as<double>();
+      MS_CUDA(g, cudaMemsetAsync(thist_dev, 0, (size_t)(o.outer_maxit + 1) * sizeof(double), stream));
+    }
     SweepArgs sa;
     sa.g = g->geo();
     sa.f = f;
@@ -762,6 +771,7 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
     ca.counter = &ctl->counter;
     ca.k_dev = &ctl->k_dev;
     ca.hist = hist_dev;
+    ca.thist = thist_dev;
     ca.outer_tol = o.outer_tol;
     ca.outer_maxit = o.outer_maxit;
     ca.time_budget_ns = o.time_limit_ms > 0.0 ? (unsigned long long)(o.time_limit_ms * 1.0e6) : 0ull;
@@ -1077,6 +1087,10 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
     }
     if (o.res_hist) {
       MS_CUDA(g, cudaMemcpyAsync(o.res_hist, hist_dev, (size_t)g->nrhs * (o.outer_maxit + 1) * sizeof(double),
+                                 cudaMemcpyDeviceToHost, stream));
+    }
+    if (o.time_hist) {
+      MS_CUDA(g, cudaMemcpyAsync(o.time_hist, thist_dev, (size_t)(o.outer_maxit + 1) * sizeof(double),
                                  cudaMemcpyDeviceToHost, stream));
     }
   }

@@ -112,6 +112,7 @@ struct CheckArgs {
   unsigned int* counter;
   int* k_dev;
   double* hist;  // [nrhs][outer_maxit+1] or null
+  double* thist;  // [outer_maxit+1] or null: ms since the first stop test, per stop test
   double outer_tol;
   int outer_maxit;
   unsigned long long time_budget_ns;  // 0 = none: else active rhs stop (kErrTimeout) once spent

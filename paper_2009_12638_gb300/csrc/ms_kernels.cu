@@ -179,6 +179,7 @@ __global__ void check_kernel(const CheckArgs a) {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
     if (*a.t_start == 0ull) *a.t_start = now;
     timed_out = (a.time_budget_ns && now - *a.t_start > a.time_budget_ns) ? 1 : 0;
+    if (a.thist && k <= a.outer_maxit) a.thist[k] = (double)(now - *a.t_start) * 1e-6;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;

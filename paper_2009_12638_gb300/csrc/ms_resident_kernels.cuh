@@ -331,6 +331,7 @@ __device__ __forceinline__ void flow_decide(const FlowArgs& fa, int kr) {
     if (*c.t_start == 0ull) *c.t_start = now;
     timed_out = (c.time_budget_ns && now - *c.t_start > c.time_budget_ns) ? 1 : 0;
     if (timed_out) atomicOr(c.err, kErrTimeout);
+    if (c.thist && k <= c.outer_maxit) c.thist[k] = (double)(now - *c.t_start) * 1e-6;
   }
   timed_out = __shfl_sync(0xffffffffu, timed_out, 0);
   int done = 1;

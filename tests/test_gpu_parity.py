@@ -412,3 +412,18 @@ def test_resident_refuses_blocks_that_do_not_fit():
     with pytest.raises(Exception):
         big.solve(bnd=torch.zeros(1, big.nbnd, dtype=torch.float64, device="cuda"), precision="mixed",
                   engine="resident", outer_maxit=1)
+
+
+@pytest.mark.parametrize("persistent", [True, False])
+def test_residual_versus_time_history(persistent):
+    """history=True records rho_k and the device time of its stop test
+    (measured from the first one): the residual-versus-time curve."""
+    cfg = inputs.make_config("laplace256_u11", scale=4)
+    g = make_grid(cfg["nx"], cfg["ny"], cfg["nz"], 1, cfg["cx"], cfg["cy"], cfg["cz"])
+    x, st = g.solve(bnd=cuda(cfg["bnd"]), precision="mixed", engine="resident", persistent=persistent, history=True)
+    k = st.outer_its
+    t = st.history_ms[: k + 1]
+    h = st.history[0][: k + 1]
+    assert st.status == 0 and h[-1] < 1e-8 <= h[-2]
+    assert t[0] == 0.0 and (np.diff(t) >= 0.0).all() and t[-1] > 0.0
+    assert t[-1] <= st.time_ms
