@@ -117,7 +117,7 @@ typedef struct {
                             method of the paper's own runs (section 3.2), classical Gram-Schmidt
                             Arnoldi; inner_rtol tests its residual estimate, inner_maxit caps its
                             Arnoldi steps.  Runs on the scalar streaming engine (engine 0 or 1). */
-  int gmres_restart;     /* GMRES basis vectors per cycle, 1..16 (default 10) */
+  int gmres_restart;     /* GMRES basis vectors per cycle, 1..50 (default 10) */
   double* time_hist;     /* HOST, optional (sync mode): [outer_maxit+1] device time in ms, measured from
                             the first stop test, at which the stop test of x^k ran -- with res_hist the
                             residual-versus-time curve the paper plots */

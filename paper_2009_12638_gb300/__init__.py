@@ -204,7 +204,7 @@ class Grid:
         layout row, see resident_variants(); -1 = tuned), inner_adapt (sync:
         choose the inner tolerance at run time), overlap (sync: blocks extended
         by this many points per face, streaming engine), inner ('cg'|'gmres'),
-        gmres_restart (GMRES basis size per cycle, 1..16).
+        gmres_restart (GMRES basis size per cycle, 1..50).
         """
         return self._call(self._lib.ms_solve, f, bnd, x0, out, history, opts)
 

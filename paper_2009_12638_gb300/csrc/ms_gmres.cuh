@@ -9,6 +9,10 @@
 //   pass 1: w = A_ii v_j, stored as the next basis vector; h_ij = w.v_i, i <= j
 //   pass 2: w -= sum_i h_ij v_i; ||w||^2
 //
+// Projections are reduced kGmresChunk at a time: steps j < kGmresChunk (every
+// step when m <= 16) take the single reduction above; a later step re-reads
+// the stored w once per further chunk of kGmresChunk basis vectors, so
+// registers and shared memory stay bounded up to m = kGmresMaxRestart.
 // Basis vectors are stored unnormalised, v_i = sigma_i u_i (sigma_i =
 // 1/||w|| of the step that made it), so normalising costs no pass.  Thread 0
 // keeps the Hessenberg column, the Givens rotations, the residual estimate
@@ -22,13 +26,16 @@
 
 namespace ms {
 
-constexpr int kGmresMaxRestart = 16;
+constexpr int kGmresMaxRestart = 50;
+constexpr int kGmresChunk = 16;  // projections per cluster reduction
 
 template <typename T>
 struct GmresVecs {
-  T* r;                          // block residual on entry (left unchanged)
-  T* d;                          // correction
-  T* u[kGmresMaxRestart + 1];    // basis vectors (unnormalised)
+  T* r;                // block residual on entry (left unchanged)
+  T* d;                // correction
+  T* u0;               // basis vectors u_0 .. u_m (unnormalised), `stride` apart
+  long long stride;
+  __device__ __forceinline__ T* u(int i) const { return u0 + (long long)i * stride; }
 };
 
 // slot layout: r, d, u_0 .. u_m (m + 3 vectors of vec_stride elements)
@@ -36,18 +43,13 @@ template <typename T>
 __device__ __forceinline__ GmresVecs<T> gmres_slot_vecs(void* scratch, long long vec_stride, unsigned slot,
                                                         int restart) {
   T* base = reinterpret_cast<T*>(scratch) + (long long)slot * (restart + 3) * vec_stride;
-  GmresVecs<T> v;
-  v.r = base;
-  v.d = base + vec_stride;
-#pragma unroll
-  for (int i = 0; i <= kGmresMaxRestart; ++i) v.u[i] = base + (long long)(2 + (i <= restart ? i : 0)) * vec_stride;
-  return v;
+  return GmresVecs<T>{base, base + vec_stride, base + 2 * vec_stride, vec_stride};
 }
 
 // Shared state of one cluster's GMRES (thread 0 writes the scalars).
 struct GmresSmem {
-  double slots[kGmresMaxRestart + 1][kMaxCluster];
-  double wsum[kGmresMaxRestart + 1][32];
+  double slots[2][kGmresChunk][kMaxCluster];  // consecutive chunk reductions alternate buffers
+  double wsum[kGmresChunk][32];
   double H[kGmresMaxRestart + 1][kGmresMaxRestart];  // rotated Hessenberg columns (upper triangle)
   double cs[kGmresMaxRestart], sn[kGmresMaxRestart];
   double g[kGmresMaxRestart + 1];
@@ -77,7 +79,7 @@ __device__ __forceinline__ T block_apply(const T* u, const Slab& sl, int c, int 
 template <typename T, int NT>
 __device__ int block_gmres(const GmresVecs<T>& v, int restart, const Slab& sl, double gamma0, double inner_rtol,
                            int inner_maxit, RedSmem& sm, GmresSmem& gs, unsigned rank, unsigned csize) {
-  constexpr int NV = kGmresMaxRestart + 1;
+  constexpr int C = kGmresChunk;
   const int tid = threadIdx.x;
   if (tid == 0) {
     gs.beta0 = sqrt(gamma0);
@@ -92,11 +94,12 @@ __device__ int block_gmres(const GmresVecs<T>& v, int restart, const Slab& sl, d
     // ---- residual of the current iterate into u_0: r (first cycle, d = 0) or r - A d
     {
       T acc = 0;
+      T* u0 = v.u(0);
       for (int c = tid; c < sl.plane; c += NT)
         for (int z = sl.z0; z < sl.z1; ++z) {
           const int i = z * sl.plane + c;
           const T w = first_cycle ? v.r[i] : v.r[i] - block_apply(v.d, sl, c, z);
-          v.u[0][i] = w;
+          u0[i] = w;
           acc += w * w;
         }
       const T red[1] = {acc};
@@ -115,47 +118,58 @@ __device__ int block_gmres(const GmresVecs<T>& v, int restart, const Slab& sl, d
     }
     if (gs.done) break;
     for (int j = 0; j < restart; ++j) {
-      // ---- pass 1: w = A v_j into u_{j+1}; projections on u_0..u_j
-      {
-        T hp[NV];
+      const int nch = j / C + 1;  // chunks of projections in this step
+      T* un = v.u(j + 1);
+      // ---- pass 1: w = A v_j into u_{j+1}; projections on u_0..u_{min(j, C-1)}
+      // ---- pass 1b (j >= C): projections of the stored w on the further chunks
+      for (int ch = 0; ch < nch; ++ch) {
+        const int q0 = ch * C;
+        T hp[C];
 #pragma unroll
-        for (int q = 0; q < NV; ++q) hp[q] = 0;
+        for (int q = 0; q < C; ++q) hp[q] = 0;
         const T sj = (T)gs.sigma[j];
-        const T* uj = v.u[j];
-        T* un = v.u[j + 1];
+        const T* uj = v.u(j);
         for (int c = tid; c < sl.plane; c += NT)
           for (int z = sl.z0; z < sl.z1; ++z) {
             const int i = z * sl.plane + c;
-            const T w = sj * block_apply(uj, sl, c, z);
-            un[i] = w;
+            T w;
+            if (ch == 0) {
+              w = sj * block_apply(uj, sl, c, z);
+              un[i] = w;
+            } else {
+              w = un[i];
+            }
 #pragma unroll
-            for (int q = 0; q < NV; ++q)
-              if (q <= j) hp[q] += w * v.u[q][i];
+            for (int q = 0; q < C; ++q)
+              if (q0 + q <= j) hp[q] += w * v.u(q0 + q)[i];
           }
-        cluster_reduce<NT, NV>(hp, gs.slots, gs.wsum, rank, csize, [&](double (&t)[NV]) {
-          for (int q = 0; q <= j; ++q) {
-            gs.H[q][j] = gs.sigma[q] * t[q];          // h_qj = w . v_q
-            gs.coef[q] = gs.H[q][j] * gs.sigma[q];    // on u_q in pass 2
+        cluster_reduce<NT, C>(hp, gs.slots[ch & 1], gs.wsum, rank, csize, [&](double (&t)[C]) {
+          for (int q = 0; q < C && q0 + q <= j; ++q) {
+            gs.H[q0 + q][j] = gs.sigma[q0 + q] * t[q];           // h_qj = w . v_q
+            gs.coef[q0 + q] = gs.H[q0 + q][j] * gs.sigma[q0 + q];  // on u_q in pass 2
           }
         });
       }
-      // ---- pass 2: w -= sum_q h_qj v_q, ||w||^2
+      // ---- pass 2: w -= sum_q h_qj v_q (one pass per chunk), ||w||^2 in the last
       {
-        T cq[NV];
-#pragma unroll
-        for (int q = 0; q < NV; ++q) cq[q] = q <= j ? (T)gs.coef[q] : (T)0;
-        T* un = v.u[j + 1];
         T acc = 0;
-        for (int c = tid; c < sl.plane; c += NT)
-          for (int z = sl.z0; z < sl.z1; ++z) {
-            const int i = z * sl.plane + c;
-            T w = un[i];
+        for (int ch = 0; ch < nch; ++ch) {
+          const int q0 = ch * C;
+          const bool last = ch == nch - 1;
+          T cq[C];
 #pragma unroll
-            for (int q = 0; q < NV; ++q)
-              if (q <= j) w -= cq[q] * v.u[q][i];
-            un[i] = w;
-            acc += w * w;
-          }
+          for (int q = 0; q < C; ++q) cq[q] = q0 + q <= j ? (T)gs.coef[q0 + q] : (T)0;
+          for (int c = tid; c < sl.plane; c += NT)
+            for (int z = sl.z0; z < sl.z1; ++z) {
+              const int i = z * sl.plane + c;
+              T w = un[i];
+#pragma unroll
+              for (int q = 0; q < C; ++q)
+                if (q0 + q <= j) w -= cq[q] * v.u(q0 + q)[i];
+              un[i] = w;
+              if (last) acc += w * w;
+            }
+        }
         const T red[1] = {acc};
         cluster_reduce<NT, 1>(red, sm.slots[1], sm.wsum, rank, csize, [&](double (&t)[1]) {
           const double hn = sqrt(t[0]);
@@ -180,7 +194,7 @@ __device__ int block_gmres(const GmresVecs<T>& v, int restart, const Slab& sl, d
       }
       if (gs.cycle_end) break;
     }
-    // ---- y = R^{-1} g, then d (+)= sum_q y_q v_q
+    // ---- y = R^{-1} g, then d (+)= sum_q y_q v_q (one pass per chunk)
     if (tid == 0) {
       const int k = gs.k;
       double y[kGmresMaxRestart];
@@ -189,25 +203,30 @@ __device__ int block_gmres(const GmresVecs<T>& v, int restart, const Slab& sl, d
         for (int c = q + 1; c < k; ++c) s -= gs.H[q][c] * y[c];
         y[q] = gs.H[q][q] != 0.0 ? s / gs.H[q][q] : 0.0;
       }
-      for (int q = 0; q < NV; ++q) gs.coef[q] = q < k ? y[q] * gs.sigma[q] : 0.0;
+      for (int q = 0; q <= kGmresMaxRestart; ++q) gs.coef[q] = q < k ? y[q] * gs.sigma[q] : 0.0;
       // the cycle's last estimate decides whether another cycle runs
       if (fabs(gs.g[k]) <= gs.stop || gs.total >= inner_maxit) gs.done = 1;
     }
     __syncthreads();
     {
-      T cq[NV];
-#pragma unroll
-      for (int q = 0; q < NV; ++q) cq[q] = (T)gs.coef[q];
       const int k = gs.k;
-      for (int c = tid; c < sl.plane; c += NT)
-        for (int z = sl.z0; z < sl.z1; ++z) {
-          const int i = z * sl.plane + c;
-          T acc = 0;
+      const int nch = k > C ? (k + C - 1) / C : 1;
+      for (int ch = 0; ch < nch; ++ch) {
+        const int q0 = ch * C;
+        const bool fresh = first_cycle && ch == 0;
+        T cq[C];
 #pragma unroll
-          for (int q = 0; q < NV; ++q)
-            if (q < k) acc += cq[q] * v.u[q][i];
-          v.d[i] = first_cycle ? acc : v.d[i] + acc;
-        }
+        for (int q = 0; q < C; ++q) cq[q] = q0 + q < k ? (T)gs.coef[q0 + q] : (T)0;
+        for (int c = tid; c < sl.plane; c += NT)
+          for (int z = sl.z0; z < sl.z1; ++z) {
+            const int i = z * sl.plane + c;
+            T acc = 0;
+#pragma unroll
+            for (int q = 0; q < C; ++q)
+              if (q0 + q < k) acc += cq[q] * v.u(q0 + q)[i];
+            v.d[i] = fresh ? acc : v.d[i] + acc;
+          }
+      }
     }
     first_cycle = false;
     if (gs.done) break;

@@ -156,7 +156,7 @@ def test_solve_rejects_bad_arguments_before_device_work(lib):
         o2.inner_adapt, o2.mode = 1, 1
         assert lib.ms_solve(h, None, None, dummy, ctypes.byref(o2), None, None) == _lib.MS_ERR_ARG
         # GMRES: restart range, sync mode, streaming engine
-        for fields in [dict(inner_method=1, gmres_restart=0), dict(inner_method=1, gmres_restart=17),
+        for fields in [dict(inner_method=1, gmres_restart=0), dict(inner_method=1, gmres_restart=51),
                        dict(inner_method=1, mode=1), dict(inner_method=1, engine=2)]:
             o2 = _lib.Opts()
             lib.ms_default_opts(ctypes.byref(o2))

@@ -86,3 +86,30 @@ def test_gmres_with_overlap_matches_oracle():
     ref = oracle.solve(nx, ny, nz, cx, cy, cz, bnd=bnd[0], outer_tol=0.0, outer_maxit=2, inner="gmres", restart=10,
                        overlap=2)
     assert rel_inf(x.cpu().numpy()[0], ref["x"]) <= 1e-10
+
+
+@pytest.mark.parametrize("restart", [30, 50])
+def test_fp64_long_restart_gmres_matches_oracle(restart):
+    """Restarts past one projection chunk (16): PETSc's default GMRES(30) and
+    the largest basis, with a tight inner tolerance so that steps j >= 16 (and,
+    at 30, a restart) run; several chunks of projections per step."""
+    nx, ny, nz, cx, cy, cz = CASES[1]
+    bnd = np.random.default_rng(98 + restart).uniform(-1, 1, size=(1, inputs.boundary_size(nx, ny, nz)))
+    g = make(nx, ny, nz, 1, cx, cy, cz)
+    x, st = g.solve(bnd=cuda(bnd), precision="fp64", inner="gmres", gmres_restart=restart, inner_maxit=60,
+                    inner_rtol=1e-10, outer_tol=0.0, outer_maxit=2)
+    ref = oracle.solve(nx, ny, nz, cx, cy, cz, bnd=bnd[0], inner_rtol=1e-10, inner_maxit=60, outer_tol=0.0,
+                       outer_maxit=2, inner="gmres", restart=restart)
+    assert ref["inner_its"] > 2 * 12 * 16  # on average the blocks go past the first chunk
+    assert rel_inf(x.cpu().numpy()[0], ref["x"]) <= 1e-9
+    assert abs(st.inner_its - ref["inner_its"]) <= 2 * 12
+
+
+def test_mixed_gmres30_sweep_close_to_oracle():
+    nx, ny, nz, cx, cy, cz = CASES[0]
+    bnd = np.random.default_rng(99).uniform(-1, 1, size=(1, inputs.boundary_size(nx, ny, nz)))
+    g = make(nx, ny, nz, 1, cx, cy, cz)
+    x, st = g.solve(bnd=cuda(bnd), precision="mixed", inner="gmres", gmres_restart=30, outer_tol=0.0,
+                    outer_maxit=1)
+    ref = oracle.solve(nx, ny, nz, cx, cy, cz, bnd=bnd[0], outer_tol=0.0, outer_maxit=1, inner="gmres", restart=30)
+    assert rel_inf(x.cpu().numpy()[0], ref["x"]) <= 5e-4
