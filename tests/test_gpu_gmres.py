@@ -113,3 +113,26 @@ def test_mixed_gmres30_sweep_close_to_oracle():
                     outer_maxit=1)
     ref = oracle.solve(nx, ny, nz, cx, cy, cz, bnd=bnd[0], outer_tol=0.0, outer_maxit=1, inner="gmres", restart=30)
     assert rel_inf(x.cpu().numpy()[0], ref["x"]) <= 5e-4
+
+
+@pytest.mark.parametrize("cuts", [
+    ([0, 2, 4, 6], [0, 2, 4], [0, 2, 4]),          # 2^3 blocks: Krylov space of dimension <= 8
+    ([0, 1, 2, 3], [0, 1, 2], [0, 1, 2]),          # 1^3 blocks: A_ii = 6, exact after one step
+])
+def test_gmres_breakdown_on_small_blocks_matches_oracle(cuts):
+    """A restart larger than the block's Krylov space: the Arnoldi step that
+    reaches an invariant subspace has h_{j+1,j} = 0 (the lucky breakdown), the
+    cycle ends with the exact block solve, and no further step runs."""
+    cx, cy, cz = cuts
+    nx, ny, nz = cx[-1], cy[-1], cz[-1]
+    bnd = np.random.default_rng(100 + nx).uniform(-1, 1, size=(1, inputs.boundary_size(nx, ny, nz)))
+    g = make(nx, ny, nz, 1, cx, cy, cz)
+    x, st = g.solve(bnd=cuda(bnd), precision="fp64", inner="gmres", gmres_restart=30, inner_maxit=40,
+                    inner_rtol=1e-14, outer_tol=0.0, outer_maxit=3)
+    ref = oracle.solve(nx, ny, nz, cx, cy, cz, bnd=bnd[0], inner_rtol=1e-14, inner_maxit=40, outer_tol=0.0,
+                       outer_maxit=3, inner="gmres", restart=30)
+    assert rel_inf(x.cpu().numpy()[0], ref["x"]) <= 1e-10
+    nblk = (len(cx) - 1) * (len(cy) - 1) * (len(cz) - 1)
+    bsz = (cx[1] - cx[0]) * (cy[1] - cy[0]) * (cz[1] - cz[0])
+    assert ref["inner_its"] <= 3 * nblk * bsz  # finite termination in every block solve
+    assert abs(st.inner_its - ref["inner_its"]) <= 3 * nblk
