@@ -170,7 +170,7 @@ def run_reference(args):
     threads = oracle.max_threads()
     sweeps = 1
     for _ in range(args.warmup):
-        pass  # the oracle has no warm-up state; warm-up steps are skipped deliberately
+        oracle_sample(cfg, sweeps, threads)  # untimed
     total_lups, total_s = 0, 0.0
     for _ in range(args.steps):
         lups, el = oracle_sample(cfg, sweeps, threads)
