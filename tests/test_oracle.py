@@ -169,6 +169,91 @@ def test_block_cg_finite_termination(oracle_mod):
     np.testing.assert_allclose(d.ravel(), np.linalg.solve(A, r0.ravel()), rtol=1e-10, atol=1e-12)
 
 
+def krylov_basis(A, r0, m):
+    """Orthonormal basis of K_m(A, r0) = span{r0, A r0, ..., A^(m-1) r0} by Arnoldi
+    with two Gram-Schmidt passes per vector (numpy, no oracle code)."""
+    Q = np.zeros((r0.size, m))
+    Q[:, 0] = r0 / np.linalg.norm(r0)
+    for j in range(1, m):
+        w = A @ Q[:, j - 1]
+        for _ in range(2):
+            w = w - Q[:, :j] @ (Q[:, :j].T @ w)
+        Q[:, j] = w / np.linalg.norm(w)
+    return Q
+
+
+def cg_minimisers(A, r0, mmax):
+    """For m = 1..mmax the d_m in K_m(A, r0) minimising the A-norm of the error
+    ||A^-1 r0 - d||_A, i.e. the Galerkin solution d_m = Q (Q^T A Q)^-1 Q^T r0 --
+    the characterisation of the m-th CG iterate from d = 0 (section 2.2)."""
+    out = []
+    for m in range(1, mmax + 1):
+        Q = krylov_basis(A, r0, m)
+        out.append(Q @ np.linalg.solve(Q.T @ A @ Q, Q.T @ r0))
+    return out
+
+
+@pytest.mark.parametrize("shape", [(5, 6, 7), (8, 8, 8), (9, 3, 4)])
+def test_block_cg_truncated_iterates_minimise_the_a_norm_error(oracle_mod, shape):
+    """The hot path always stops CG long before finite termination (64^3 blocks,
+    cap 50), so the truncated iterate itself is pinned: with inner_rtol = 0 the
+    solve takes exactly m = inner_maxit steps and returns the A-norm minimiser
+    over K_m(A_ii, r_0), and its r is the true residual r_0 - A_ii d."""
+    bx, by, bz = shape
+    A = kron_laplacian(bx, by, bz).toarray()
+    r0 = rng(40 + bx).standard_normal(A.shape[0])
+    ref = cg_minimisers(A, r0, 12)
+    for m in range(1, 13):
+        d, r, its = oracle_mod.block_cg(r0.reshape(bz, by, bx), 0.0, m)
+        assert its == m
+        np.testing.assert_allclose(d.ravel(), ref[m - 1], rtol=0, atol=1e-10 * np.abs(ref[m - 1]).max())
+        np.testing.assert_allclose(r.ravel(), r0 - A @ d.ravel(), rtol=0, atol=1e-12 * np.abs(r0).max())
+
+
+@pytest.mark.parametrize("target", [3, 7, 11])
+def test_block_cg_stops_at_the_first_step_meeting_the_tolerance(oracle_mod, target):
+    """With inner_rtol > 0 the returned m is the first m with
+    ||r_0 - A d_m|| <= inner_rtol ||r_0||, d_m the Krylov minimiser (the CG
+    residual norm need not decrease monotonically, so 'first' matters); the
+    tolerance is placed just above the target step's ratio and far (relative
+    1e-6) from every other step's, so rounding cannot move the stop.  A cap at
+    the stop step gives the same m; a cap one below it gives the cap."""
+    bx, by, bz = 6, 7, 5
+    A = kron_laplacian(bx, by, bz).toarray()
+    r0 = rng(50).standard_normal(A.shape[0])
+    ratios = np.array([np.linalg.norm(r0 - A @ d) for d in cg_minimisers(A, r0, 14)]) / np.linalg.norm(r0)
+    rtol = ratios[target - 1] * (1 + 1e-7)
+    first = 1 + int(np.argmax(ratios <= rtol))
+    assert np.all(np.abs(ratios / rtol - 1) > 1e-8)
+    d, r, m = oracle_mod.block_cg(r0.reshape(bz, by, bx), rtol, 200)
+    assert m == first
+    assert np.linalg.norm(r) <= rtol * np.linalg.norm(r0)
+    _, _, m_cap = oracle_mod.block_cg(r0.reshape(bz, by, bx), rtol, first)
+    assert m_cap == first
+    _, _, m_short = oracle_mod.block_cg(r0.reshape(bz, by, bx), rtol, first - 1)
+    assert m_short == first - 1
+
+
+def test_block_cg_tolerance_tie_stops(oracle_mod):
+    """The stop test is ||r_m|| <= inner_rtol ||r_0|| (non-strict).  Block 2x1x1
+    (A = [[6, -1], [-1, 6]]), r_0 = (1, 0): one CG step has alpha = 1/6 and
+    r_1 = (1 - 6 alpha, alpha) = (0, 1/6), so ||r_1|| = ||r_0|| / 6 exactly.
+    In FP64 every step is exact too: fl(1/6) * 6 rounds (a tie, to even) to 1,
+    and sqrt(fl(1/6)^2) = fl(1/6).  With inner_rtol = fl(1/6) the test is a tie:
+    the solve must stop after one step.  One ulp lower it must take the second
+    step (which solves the 2x2 system exactly)."""
+    sixth = 1.0 / 6.0
+    assert sixth * 6.0 == 1.0 and np.sqrt(sixth * sixth) == sixth
+    r0 = np.array([[[1.0, 0.0]]])
+    d, r, m = oracle_mod.block_cg(r0, sixth, 50)
+    assert m == 1
+    np.testing.assert_array_equal(d.ravel(), [sixth, 0.0])
+    np.testing.assert_array_equal(r.ravel(), [0.0, sixth])
+    d, r, m = oracle_mod.block_cg(r0, np.nextafter(sixth, 0.0), 50)
+    assert m == 2
+    np.testing.assert_allclose(d.ravel(), np.linalg.solve([[6.0, -1.0], [-1.0, 6.0]], [1.0, 0.0]), rtol=1e-15)
+
+
 # ---------------------------------------------------------------- outer sweeps
 def test_one_sweep_with_unit_blocks_is_point_jacobi(oracle_mod):
     """1x1x1 blocks: A_ii = [6] and one CG step is exact, so one outer sweep is
