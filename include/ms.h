@@ -83,7 +83,8 @@ typedef struct {
   int slots;             /* blocks in flight at once (clusters launched), 0 = tuned */
   int check_every;       /* sync mode: sweeps between host convergence polls, 0 = auto */
   int use_graph;         /* sync mode: replay sweeps from a captured CUDA graph (default 1) */
-  int slow_block;        /* async resilience test: this block id sleeps slow_ns per visit; -1 = none */
+  int slow_block;        /* resilience test (asynchronous mode and the persistent synchronous launch):
+                            this block id sleeps slow_ns per visit; -1 = none */
   int slow_ns;           /*   bounded __nanosleep budget per visit of slow_block */
   double* res_hist;      /* HOST, optional: [nrhs][outer_maxit+1] relative residual per sweep
                             (sync mode; entries after each rhs stops are left untouched) */
@@ -121,6 +122,11 @@ typedef struct {
   double* time_hist;     /* HOST, optional (sync mode): [outer_maxit+1] device time in ms, measured from
                             the first stop test, at which the stop test of x^k ran -- with res_hist the
                             residual-versus-time curve the paper plots */
+  int wait_polls;        /* persistent synchronous launch: polls a cluster may spend, summed over the
+                            launch, in its bounded waits for a neighbour's progress flag or a stop
+                            decision; when they run out the solve ends with MS_ERR_TIMEOUT and x holds
+                            the last complete iterate.  0 (default) = 2^24 polls (backing off to
+                            ~1 us each) */
 } ms_opts;
 
 typedef struct {
@@ -196,20 +202,56 @@ MS_API int ms_residual(ms_grid* grid, const double* f, const double* bnd, const 
  * device).  lam is [nrhs][nz][ny][nx] (device). */
 MS_API int ms_face_gather(ms_grid* grid, const double* lam, double* grad_bnd, void* stream);
 
+/* The raw sums behind ms_residual, per rhs, left on the device:
+ *   rr_out DEVICE [nrhs] or NULL: sum over this grid's points of (bhat - A x)^2;
+ *   bb_out DEVICE [nrhs] or NULL: sum of bhat^2 (bhat = f + lift(bnd));
+ * at least one must be non-NULL; FP64, summed in a fixed order (the result
+ * does not depend on the stream or the launch).  Section 3 assembles the
+ * global residual from per-block partial sums; a grid that is one shard of a
+ * larger problem (its neighbours' values given as Dirichlet data in bnd)
+ * returns its share of the global sums, to be added over the shards.  Ready
+ * on `stream`'s timeline; no host synchronisation. */
+MS_API int ms_norms(ms_grid* grid, const double* f, const double* bnd, const double* x, double* rr_out,
+                    double* bb_out, void* stream);
+
+/* One synchronous outer sweep (section 3: X_i <- X_i + A_ii^{-1}(B_i - A X)_i
+ * for every block i, all blocks reading the same x^k), for callers that run
+ * the outer loop themselves -- a grid that is one shard of a problem split
+ * over several GPUs, whose neighbouring shards' boundary planes enter as the
+ * Dirichlet data in bnd (section 3's halo swap between block groups):
+ *   f, bnd: as ms_solve (device; may be NULL);
+ *   x_in:   [nrhs][nz][ny][nx] x^k (device, read only);
+ *   x_out:  [nrhs][nz][ny][nx] receives x^{k+1} (device; must not overlap x_in);
+ *   rr_out: DEVICE [nrhs] or NULL: sum of (bhat - A x^k)^2 over this grid, as
+ *           ms_norms (the residual the stop rule of section 2.1 tests on x^k);
+ *   opts:   HOST or NULL; precision, inner_rtol, inner_maxit, overlap,
+ *           inner_method, gmres_restart and the launch-shape fields are used;
+ *           mode must be MS_MODE_SYNC and inner_adapt 0;
+ *   stats:  HOST or NULL.  NULL: nothing waits for the GPU (the results are
+ *           ready on `stream`'s timeline).  Non-NULL: synchronises `stream` and
+ *           fills inner_its, lups, time_ms, the launch shape, outer_its = 1 and
+ *           rel_residual = that of x^k against this grid's own ||bhat||.
+ * The launch shape is the one a solve of the same problem measured (ms_solve
+ * caches it per handle), else the model's first choice.  The inner solves use
+ * the same kernels and FP32 scaling as ms_solve, so a sweep here equals a
+ * sweep of ms_solve on the same data. */
+MS_API int ms_sweep(ms_grid* grid, const double* f, const double* bnd, const double* x_in, double* x_out,
+                    double* rr_out, const ms_opts* opts, ms_stats* stats, void* stream);
+
 /* The largest nrhs ms_residual_noalloc accepts (its scratch has a fixed size). */
 #define MS_NOALLOC_MAX_RHS 1024
 
 /* ms_residual without any device allocation.  (The paper has no counterpart:
  * this is an interface for callers, not a step of the method.)
  *
- * For callers that cannot call cudaMalloc where they need the residual: code
- * running while a CUDA graph is captured (an allocation there breaks the
- * capture), latency-critical loops that cannot absorb cudaMalloc's implicit
- * device synchronisation, or applications whose device memory is owned by
- * their own pool allocator.  ms_residual allocates a per-handle workspace on
- * first use; this function uses instead a fixed 1 MiB array of partial sums
- * compiled into the library (a static device array that every GPU loading
- * the library holds until the process exits).
+ * For callers that cannot call cudaMalloc where they need the residual:
+ * latency-critical loops that cannot absorb cudaMalloc's implicit device
+ * synchronisation, or applications whose device memory is owned by their own
+ * pool allocator and that may not allocate behind its back.  ms_residual
+ * allocates a per-handle workspace on first use; this function uses instead
+ * a fixed 1 MiB array of partial sums compiled into the library (a static
+ * device array that every GPU loading the library holds until the process
+ * exits).
  *   f, bnd, x: as ms_residual (device; f and bnd may be NULL);
  *   rel_out:   DEVICE [nrhs] doubles, ||bhat - A x||_2 / ||bhat||_2 per rhs
  *              (the absolute norm where ||bhat|| = 0), ready on `stream`'s
@@ -217,8 +259,11 @@ MS_API int ms_face_gather(ms_grid* grid, const double* lam, double* grad_bnd, vo
  * Limits and caveats:
  *   - nrhs must be <= MS_NOALLOC_MAX_RHS, else MS_ERR_ARG with a message;
  *   - the first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture on that device;
+ *     (cudaGetSymbolAddress) with that device current and caches it; make
+ *     that first call before any stream capture on that device;
+ *   - the cached address is not looked up again: after cudaDeviceReset on a
+ *     device, do not call this function on that device again in the same
+ *     process (the address may have changed);
  *   - every call on a device shares the one array: calls whose work can
  *     overlap on the GPU (unordered streams) race on it and must be
  *     serialised by the caller.  Each call writes all the scratch it reads,
@@ -226,19 +271,21 @@ MS_API int ms_face_gather(ms_grid* grid, const double* lam, double* grad_bnd, vo
 MS_API int ms_residual_noalloc(ms_grid* grid, const double* f, const double* bnd, const double* x, double* rel_out,
                                void* stream);
 
-/* Free the handle and its device workspace.  Synchronises the device work
- * the handle issued.  NULL is accepted. */
 /* Row v of the resident engine's variant table (no counterpart in the paper:
  * the table lists the on-chip layouts of one block's CG state that the
  * autotuner chooses from).  threads: threads per CTA; strips: 4-point x-strips
  * a thread owns per plane; planes: z-planes a CTA holds at most; d_smem: the
  * correction d lives in shared memory (else registers); q_regs: A p is kept
  * in registers between the two halves of a CG iteration (one stencil per
- * iteration instead of two, bit-identical results).  Any output pointer may
- * be NULL.  Returns MS_OK, or MS_ERR_ARG if v is
- * outside [0, count); *count (if non-NULL) always receives the number of
- * rows.  Host only, no device work. */
-MS_API int ms_resident_variant(int v, int* count, int* threads, int* strips, int* planes, int* d_smem, int* q_regs);
+ * iteration instead of two, bit-identical results); one_reduction: the
+ * single-reduction CG (Chronopoulos and Gear's rearrangement of CG: one
+ * cluster-wide reduction of r.r and r.A r per iteration instead of two, the
+ * same iterates in exact arithmetic; p, A p and A r in registers, r and d in
+ * shared memory).  Any output pointer may be NULL.  Returns MS_OK, or
+ * MS_ERR_ARG if v is outside [0, count); *count (if non-NULL) always receives
+ * the number of rows.  Host only, no device work. */
+MS_API int ms_resident_variant(int v, int* count, int* threads, int* strips, int* planes, int* d_smem, int* q_regs,
+                               int* one_reduction);
 
 /* One global conjugate-gradient solve of A x = f + lift(bnd) on the whole
  * grid, in FP64, with no block splitting: the single-matrix Krylov method the
@@ -260,6 +307,8 @@ MS_API int ms_resident_variant(int v, int* count, int* threads, int* strips, int
 MS_API int ms_gcg_solve(ms_grid* grid, const double* f, const double* bnd, double* x, const ms_opts* opts,
                         ms_stats* stats, void* stream);
 
+/* Free the handle and its device workspace.  Synchronises the device work
+ * the handle issued.  NULL is accepted. */
 MS_API int ms_destroy(ms_grid* grid);
 
 /* Message for the last failure on this handle (or of ms_create_grid when

@@ -36,17 +36,18 @@ def boundary_size(nx: int, ny: int, nz: int) -> int:
 def resident_variants():
     """Rows of the resident engine's layout table (ms_resident_variant): a list
     of dicts with threads, strips (4-point x-strips per thread and plane),
-    planes (z-planes per CTA at most), d_smem, q_regs."""
+    planes (z-planes per CTA at most), d_smem, q_regs, one_reduction."""
     lib = _lib.load()
     n = ctypes.c_int(0)
-    lib.ms_resident_variant(-1, ctypes.byref(n), None, None, None, None, None)
+    lib.ms_resident_variant(-1, ctypes.byref(n), None, None, None, None, None, None)
     rows = []
     for v in range(n.value):
-        f = [ctypes.c_int(0) for _ in range(5)]
+        f = [ctypes.c_int(0) for _ in range(6)]
         rc = lib.ms_resident_variant(v, None, *[ctypes.byref(x) for x in f])
         if rc != _lib.MS_OK:
             raise MsError(f"ms_resident_variant({v}) returned {rc}")
-        rows.append(dict(zip(("threads", "strips", "planes", "d_smem", "q_regs"), (x.value for x in f))))
+        rows.append(dict(zip(("threads", "strips", "planes", "d_smem", "q_regs", "one_reduction"),
+                             (x.value for x in f))))
     return rows
 
 
@@ -88,7 +89,7 @@ def _stream_handle(device):
 def _make_opts(lib, mode="sync", precision="mixed", inner_rtol=1e-6, inner_maxit=50, outer_tol=1e-8,
                outer_maxit=100000, time_limit_ms=0.0, cluster=0, threads=0, slots=0, check_every=0, use_graph=True,
                slow_block=-1, slow_ns=0, profile=False, engine="auto", persistent="auto", variant=-1,
-               inner_adapt=False, overlap=0, inner="cg", gmres_restart=10):
+               inner_adapt=False, overlap=0, inner="cg", gmres_restart=10, wait_polls=0):
     o = _lib.Opts()
     lib.ms_default_opts(ctypes.byref(o))
     o.mode = _lib.MODE[mode] if isinstance(mode, str) else int(mode)
@@ -114,6 +115,7 @@ def _make_opts(lib, mode="sync", precision="mixed", inner_rtol=1e-6, inner_maxit
     o.overlap = int(overlap)
     o.inner_method = {"cg": 0, "gmres": 1}[inner] if isinstance(inner, str) else int(inner)
     o.gmres_restart = int(gmres_restart)
+    o.wait_polls = int(wait_polls)
     return o
 
 
@@ -204,7 +206,8 @@ class Grid:
         layout row, see resident_variants(); -1 = tuned), inner_adapt (sync:
         choose the inner tolerance at run time), overlap (sync: blocks extended
         by this many points per face, streaming engine), inner ('cg'|'gmres'),
-        gmres_restart (GMRES basis size per cycle, 1..50).
+        gmres_restart (GMRES basis size per cycle, 1..50), wait_polls
+        (persistent sync launch: poll budget of its bounded waits, 0 = default).
         """
         return self._call(self._lib.ms_solve, f, bnd, x0, out, history, opts)
 
@@ -289,6 +292,43 @@ class Grid:
             self._check(self._lib.ms_residual(self._h, _ptr(f), _ptr(bnd), _ptr(x), out,
                                               _stream_handle(self.device)))
         return np.array(list(out))
+
+    def norms(self, x, f=None, bnd=None):
+        """ms_norms: (rr, bb) device tensors [nrhs] -- sum of (bhat - A x)^2 and of
+        bhat^2 over this grid's points (FP64, fixed summation order)."""
+        f = self._field(f, "f", self.shape)
+        bnd = self._field(bnd, "bnd", (self.nrhs, self.nbnd))
+        x = self._field(x, "x", self.shape, allow_none=False)
+        rr = torch.empty(self.nrhs, dtype=torch.float64, device=self.device)
+        bb = torch.empty(self.nrhs, dtype=torch.float64, device=self.device)
+        with torch.cuda.device(self.device):
+            self._check(self._lib.ms_norms(self._h, _ptr(f), _ptr(bnd), _ptr(x), _ptr(rr), _ptr(bb),
+                                           _stream_handle(self.device)))
+        return rr, bb
+
+    def sweep(self, x_in, x_out, f=None, bnd=None, rr=None, stats=False, **opts):
+        """ms_sweep: one synchronous outer sweep, x_out = x^{k+1} from x_in = x^k.
+        Returns rr (device [nrhs], sum of (bhat - A x^k)^2 over this grid) and,
+        with stats=True, a SolveStats (that call waits for the GPU)."""
+        f = self._field(f, "f", self.shape)
+        bnd = self._field(bnd, "bnd", (self.nrhs, self.nbnd))
+        x_in = self._field(x_in, "x_in", self.shape, allow_none=False)
+        if (x_out.dtype != torch.float64 or not x_out.is_contiguous() or x_out.device != self.device
+                or x_out.numel() != self.nrhs * self.npts):
+            raise ValueError("x_out must be a contiguous float64 tensor of the grid's shape on its device")
+        if rr is None:
+            rr = torch.empty(self.nrhs, dtype=torch.float64, device=self.device)
+        o = _make_opts(self._lib, **opts)
+        st = _lib.Stats() if stats else None
+        with torch.cuda.device(self.device):
+            self._check(self._lib.ms_sweep(self._h, _ptr(f), _ptr(bnd), _ptr(x_in), _ptr(x_out), _ptr(rr),
+                                           ctypes.byref(o), ctypes.byref(st) if st is not None else None,
+                                           _stream_handle(self.device)))
+        if st is None:
+            return rr
+        return rr, SolveStats(st.status, st.outer_its, st.inner_its, st.lups, st.rel_residual, st.time_ms,
+                              st.launches, st.cluster, st.threads, st.slots, [], [], st.sweep_ms, st.sweep_launches,
+                              st.engine, st.variant, st.inner_rtol_final)
 
     def face_gather(self, lam):
         """grad_bnd[s][p] = lam[s][q(p)] (the adjoint of the boundary lift)."""

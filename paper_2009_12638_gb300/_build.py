@@ -18,7 +18,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libms.so")
 SOURCES = ["ms_api.cu", "ms_kernels.cu", "ms_async.cu", "ms_resident.cu", "ms_resident_inst0.cu",
-           "ms_resident_inst1.cu", "ms_resident_inst2.cu", "ms_resident_inst3.cu", "ms_tune.cu", "ms_noalloc.cu", "ms_gcg.cu",
+           "ms_resident_inst1.cu", "ms_resident_inst2.cu", "ms_resident_inst3.cu", "ms_resident_inst4.cu",
+           "ms_resident_inst5.cu", "ms_tune.cu", "ms_noalloc.cu", "ms_gcg.cu",
            "ms_stream4.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

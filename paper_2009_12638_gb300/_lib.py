@@ -26,7 +26,7 @@ PRECISION = {"fp64": 0, "mixed": 1}
 # Symbols declared in include/ms.h (checked by the CPU tests).
 EXPORTS = ("ms_boundary_size", "ms_default_opts", "ms_create_grid", "ms_partition", "ms_get_cuts", "ms_solve",
            "ms_solve_host", "ms_residual", "ms_face_gather", "ms_destroy", "ms_last_error",
-           "ms_residual_noalloc", "ms_resident_variant", "ms_gcg_solve")
+           "ms_residual_noalloc", "ms_resident_variant", "ms_gcg_solve", "ms_norms", "ms_sweep")
 NOALLOC_MAX_RHS = 1024
 
 
@@ -56,6 +56,7 @@ class Opts(ctypes.Structure):
         ("inner_method", ctypes.c_int),
         ("gmres_restart", ctypes.c_int),
         ("time_hist", ctypes.POINTER(ctypes.c_double)),
+        ("wait_polls", ctypes.c_int),
     ]
 
 
@@ -108,13 +109,15 @@ def load(path: str = LIB_PATH):
         lib.ms_gcg_solve.argtypes = [vp, vp, vp, vp, ctypes.POINTER(Opts), ctypes.POINTER(Stats), vp]
         lib.ms_residual.argtypes = [vp, vp, vp, vp, dp, vp]
         lib.ms_face_gather.argtypes = [vp, vp, vp, vp]
+        lib.ms_norms.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        lib.ms_sweep.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.POINTER(Opts), ctypes.POINTER(Stats), vp]
         lib.ms_residual_noalloc.argtypes = [vp, vp, vp, vp, vp, vp]
-        lib.ms_resident_variant.argtypes = [c_int, ip, ip, ip, ip, ip, ip]
+        lib.ms_resident_variant.argtypes = [c_int, ip, ip, ip, ip, ip, ip, ip]
         lib.ms_destroy.argtypes = [vp]
         lib.ms_last_error.argtypes = [vp]
         lib.ms_last_error.restype = ctypes.c_char_p
         for name in ("ms_create_grid", "ms_partition", "ms_get_cuts", "ms_solve", "ms_solve_host", "ms_residual",
-                     "ms_face_gather", "ms_destroy", "ms_residual_noalloc"):
+                     "ms_face_gather", "ms_destroy", "ms_residual_noalloc", "ms_norms", "ms_sweep", "ms_gcg_solve"):
             getattr(lib, name).restype = c_int
         _lib = lib
         return lib

@@ -160,6 +160,7 @@ extern "C" void ms_default_opts(ms_opts* o) {
   o->inner_method = 0;
   o->gmres_restart = 10;
   o->time_hist = nullptr;
+  o->wait_polls = 0;
 }
 
 static std::vector<int> equal_cuts(int n, int p) {
@@ -278,6 +279,7 @@ static int check_opts(ms_grid* g, const ms_opts& o) {
     return fail(g, MS_ERR_ARG, "opts.variant must be -1 (tuned) or 0..%d", ms::res_variant_count() - 1);
   if (o.inner_adapt != 0 && o.inner_adapt != 1) return fail(g, MS_ERR_ARG, "opts.inner_adapt must be 0 or 1");
   if (o.overlap < 0) return fail(g, MS_ERR_ARG, "opts.overlap must be >= 0");
+  if (o.wait_polls < 0) return fail(g, MS_ERR_ARG, "opts.wait_polls must be >= 0 (0 = default)");
   if (o.inner_method != 0 && o.inner_method != 1) return fail(g, MS_ERR_ARG, "opts.inner_method must be 0 (CG) or 1 (GMRES)");
   if (o.inner_method == 1 && (o.gmres_restart < 1 || o.gmres_restart > kGmresMaxRestart))
     return fail(g, MS_ERR_ARG, "opts.gmres_restart must be 1..%d", kGmresMaxRestart);
@@ -400,6 +402,181 @@ extern "C" int ms_face_gather(ms_grid* g, const double* lam, double* grad_bnd, v
   if (!g) return MS_ERR_ARG;
   if (!lam || !grad_bnd) return fail(g, MS_ERR_ARG, "ms_face_gather: NULL argument");
   MS_CUDA(g, launch_face_gather(g->geo(), lam, grad_bnd, (cudaStream_t)stream));
+  return MS_OK;
+}
+
+extern "C" int ms_norms(ms_grid* g, const double* f, const double* bnd, const double* x, double* rr_out,
+                        double* bb_out, void* stream) {
+  if (!g) return MS_ERR_ARG;
+  if (!x || (!rr_out && !bb_out))
+    return fail(g, MS_ERR_ARG, "ms_norms: x and at least one of rr_out, bb_out must be non-NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  CtlLayout L = ctl_layout(g->nrhs);
+  MS_CUDA(g, g->ctl.reserve(L.bytes));
+  double* norms = reinterpret_cast<double*>(g->ctl.as<char>() + L.off_norm);
+  int rc = run_resid(g, f, bnd, x, norms, nullptr, s);
+  if (rc != MS_OK) return rc;
+  // norms is [nrhs][2] (sum r^2, sum bhat^2): strided copies into the caller's arrays
+  if (rr_out)
+    MS_CUDA(g, cudaMemcpy2DAsync(rr_out, sizeof(double), norms, 2 * sizeof(double), sizeof(double), g->nrhs,
+                                 cudaMemcpyDeviceToDevice, s));
+  if (bb_out)
+    MS_CUDA(g, cudaMemcpy2DAsync(bb_out, sizeof(double), norms + 1, 2 * sizeof(double), sizeof(double), g->nrhs,
+                                 cudaMemcpyDeviceToDevice, s));
+  return MS_OK;
+}
+
+// One synchronous outer sweep outside ms_solve's loop: the residual of x_in
+// (norms and the FP32 scaling), then one launch of the sweep kernel that
+// ms_solve would use for this problem (its tuned shape when a solve of the
+// same problem measured one, else the model's first choice), reading x^k from
+// x_in and writing x^{k+1} to x_out.
+extern "C" int ms_sweep(ms_grid* g, const double* f, const double* bnd, const double* x_in, double* x_out,
+                        double* rr_out, const ms_opts* opts, ms_stats* st, void* stream_ptr) {
+  if (!g) return MS_ERR_ARG;
+  if (!x_in || !x_out) return fail(g, MS_ERR_ARG, "ms_sweep: x_in and x_out must be non-NULL");
+  const long long npts = g->npts();
+  const size_t xbytes = (size_t)g->nrhs * npts * sizeof(double);
+  {
+    const char* a = reinterpret_cast<const char*>(x_in);
+    const char* b = reinterpret_cast<const char*>(x_out);
+    if (a < b + xbytes && b < a + xbytes) return fail(g, MS_ERR_ARG, "ms_sweep: x_in and x_out overlap");
+  }
+  ms_opts o;
+  if (opts) o = *opts;
+  else ms_default_opts(&o);
+  int rc = check_opts(g, o);
+  if (rc != MS_OK) return rc;
+  if (o.mode != MS_MODE_SYNC || o.inner_adapt)
+    return fail(g, MS_ERR_ARG, "ms_sweep: one synchronous sweep (mode SYNC, inner_adapt 0)");
+  cudaGetLastError();
+  cudaStream_t stream = (cudaStream_t)stream_ptr;
+  const int prec = o.precision == MS_PREC_MIXED ? 1 : 0;
+  const size_t esz = prec ? sizeof(float) : sizeof(double);
+  long long maxpts = 0;
+  std::vector<Task> tasks = build_tasks(g, &maxpts, o.overlap);
+  const int ntasks = (int)tasks.size();
+  const bool gmres = o.inner_method == 1;
+  const int eff_engine = o.variant >= 0 ? 2 : ((o.overlap > 0 || gmres) ? 1 : o.engine);
+  std::vector<LaunchShape> all;
+  rc = list_shapes(g->tuner, prec, MS_MODE_SYNC, eff_engine, tasks, maxpts, o.cluster, o.threads, o.slots, o.variant,
+                   &all);
+  if (rc == 0 && gmres) {
+    all.erase(std::remove_if(all.begin(), all.end(), [](const LaunchShape& c) { return c.variant != -1; }), all.end());
+    if (all.empty()) rc = (int)cudaErrorInvalidConfiguration;
+  }
+  if (rc != 0) return fail(g, MS_ERR_CUDA, "ms_sweep: no launchable shape (%s)", cudaGetErrorString((cudaError_t)rc));
+  LaunchShape shape = all.front();
+  {
+    const std::vector<long long> sig = signature(prec, MS_MODE_SYNC, eff_engine + 10 * o.inner_method, tasks);
+    auto it = g->tuner.best.find(sig);
+    const bool requested = o.cluster || o.threads || o.slots || o.variant >= 0;
+    if (!requested && it != g->tuner.best.end()) shape = it->second;
+  }
+  long long padded = maxpts;
+  for (const Task& t : tasks) padded = std::max(padded, (long long)t.bz * t.by * 4 * ((t.bx + 3) / 4));
+  const long long vec_stride = (padded + 31) / 32 * 32;
+  const CtlLayout L = ctl_layout(g->nrhs);
+  if (shape.variant < 0) {
+    const int nvec = gmres ? o.gmres_restart + 3 : 4;
+    MS_CUDA(g, g->scratch.reserve((size_t)shape.slots * nvec * vec_stride * esz));
+  }
+  MS_CUDA(g, g->tasks.reserve(tasks.size() * sizeof(Task)));
+  MS_CUDA(g, g->partial.reserve((size_t)ntasks * sizeof(double)));
+  MS_CUDA(g, g->ctl.reserve(L.bytes));
+  char* ctlb = g->ctl.as<char>();
+  Ctl* ctl = reinterpret_cast<Ctl*>(ctlb);
+  double* norms = reinterpret_cast<double*>(ctlb + L.off_norm);
+  double* invb = reinterpret_cast<double*>(ctlb + L.off_invb);
+  unsigned long long* inner = reinterpret_cast<unsigned long long*>(ctlb + L.off_inner);
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  struct EvGuard {
+    cudaEvent_t* a;
+    cudaEvent_t* b;
+    ~EvGuard() {
+      if (*a) cudaEventDestroy(*a);
+      if (*b) cudaEventDestroy(*b);
+    }
+  } evg{&ev0, &ev1};
+  if (st) {
+    MS_CUDA(g, cudaEventCreate(&ev0));
+    MS_CUDA(g, cudaEventCreate(&ev1));
+    MS_CUDA(g, cudaEventRecord(ev0, stream));
+  }
+  MS_CUDA(g, cudaMemcpyAsync(g->tasks.p, tasks.data(), tasks.size() * sizeof(Task), cudaMemcpyHostToDevice, stream));
+  MS_CUDA(g, cudaMemsetAsync(ctlb, 0, L.bytes, stream));  // every rhs active, sweep counter k = 0
+  rc = run_resid(g, f, bnd, x_in, norms, invb, stream);
+  if (rc != MS_OK) return rc;
+  SweepArgs sa;
+  sa.g = g->geo();
+  sa.f = f;
+  sa.bnd = bnd;
+  sa.xbuf0 = const_cast<double*>(x_in);  // read only: sweep k = 0 reads buffer 0 and writes buffer 1
+  sa.xbuf1 = x_out;
+  sa.tasks = g->tasks.as<Task>();
+  sa.ntasks = ntasks;
+  sa.counter = &ctl->counter;
+  sa.rhs_state = reinterpret_cast<int*>(ctlb + L.off_state);
+  sa.all_done = &ctl->all_done;
+  sa.partial = g->partial.as<double>();
+  sa.scratch = g->scratch.p;
+  sa.vec_stride = vec_stride;
+  sa.inner_rtol = o.inner_rtol;
+  sa.inner_maxit = o.inner_maxit;
+  sa.outer_maxit = 1;  // k = 0 < 1: a full sweep, not the residual-only one
+  sa.k_dev = &ctl->k_dev;
+  sa.inner_count = inner;
+  sa.inv_bnorm = invb;
+  sa.err = &ctl->err;
+  sa.inner_rtol_rhs = nullptr;
+  sa.inner_method = o.inner_method;
+  sa.gmres_restart = o.gmres_restart;
+  if (shape.variant >= 0) MS_CUDA(g, launch_res_sweep(shape.variant, shape.cluster, shape.slots, shape.smem, sa, stream));
+  else if (shape.variant == -2) MS_CUDA(g, launch_strip_sweep(shape.threads, shape.cluster, shape.slots, sa, stream));
+  else MS_CUDA(g, launch_sweep(prec, shape.threads, shape.cluster, shape.slots, sa, stream));
+  if (rr_out)
+    MS_CUDA(g, cudaMemcpy2DAsync(rr_out, sizeof(double), norms, 2 * sizeof(double), sizeof(double), g->nrhs,
+                                 cudaMemcpyDeviceToDevice, stream));
+  if (!st) return MS_OK;
+  MS_CUDA(g, cudaEventRecord(ev1, stream));
+  std::vector<double> hn(2 * (size_t)g->nrhs);
+  std::vector<unsigned long long> hin(2 * (size_t)g->nrhs);
+  int herr = 0;
+  MS_CUDA(g, cudaMemcpyAsync(hn.data(), norms, hn.size() * sizeof(double), cudaMemcpyDeviceToHost, stream));
+  MS_CUDA(g, cudaMemcpyAsync(hin.data(), inner, hin.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                             stream));
+  MS_CUDA(g, cudaMemcpyAsync(&herr, &ctl->err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  MS_CUDA(g, cudaStreamSynchronize(stream));
+  if (herr & kErrGeometry) return fail(g, MS_ERR_CUDA, "ms_sweep: device error word 0x%x", herr);
+  float ms_el = 0.f;
+  MS_CUDA(g, cudaEventElapsedTime(&ms_el, ev0, ev1));
+  long long box_pts = 0, inner_total = 0, inner_lups = 0;
+  for (const Task& t : tasks)
+    if (t.rhs == 0) box_pts += (long long)t.bx * t.by * t.bz;
+  double relmax = 0.0;
+  for (int r = 0; r < g->nrhs; ++r) {
+    const double rel = hn[2 * r + 1] > 0.0 ? std::sqrt(hn[2 * r]) / std::sqrt(hn[2 * r + 1]) : std::sqrt(hn[2 * r]);
+    relmax = std::max(relmax, rel);
+    inner_total += (long long)hin[2 * r];
+    inner_lups += (long long)hin[2 * r + 1];
+    if (st->per_rhs_outer_its) st->per_rhs_outer_its[r] = 1;
+    if (st->per_rhs_rel) st->per_rhs_rel[r] = rel;
+  }
+  st->status = MS_OK;
+  st->outer_its = 1;
+  st->inner_its = inner_total;
+  st->lups = inner_lups + (long long)g->nrhs * box_pts;
+  st->rel_residual = relmax;  // of x_in, against this grid's own ||bhat||
+  st->time_ms = ms_el;
+  st->launches = 2;
+  st->cluster = shape.cluster;
+  st->threads = shape.threads;
+  st->slots = shape.slots;
+  st->sweep_ms = 0.0;
+  st->sweep_launches = 0;
+  st->engine = shape.variant >= 0 ? 2 : 1;
+  st->variant = shape.variant;
+  st->inner_rtol_final = o.inner_rtol;
   return MS_OK;
 }
 
@@ -560,7 +737,7 @@ extern "C" int ms_gcg_solve(ms_grid* g, const double* f, const double* bnd, doub
 }
 
 extern "C" int ms_resident_variant(int v, int* count, int* threads, int* strips, int* planes, int* d_smem,
-                                   int* q_regs) {
+                                   int* q_regs, int* one_reduction) {
   const int n = ms::res_variant_count();
   if (count) *count = n;
   if (v < 0 || v >= n) return MS_ERR_ARG;
@@ -570,7 +747,8 @@ extern "C" int ms_resident_variant(int v, int* count, int* threads, int* strips,
   if (strips) *strips = kc;
   if (planes) *planes = zs;
   if (d_smem) *d_smem = ds;
-  if (q_regs) *q_regs = qr;
+  if (q_regs) *q_regs = qr == 1 ? 1 : 0;
+  if (one_reduction) *one_reduction = qr == 2 ? 1 : 0;
   return MS_OK;
 }
 
@@ -944,7 +1122,9 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
       fa.res_cnt = reinterpret_cast<int*>(fw + o_res);
       fa.done_rel = reinterpret_cast<int*>(fw + o_done);
       fa.decided_rel = reinterpret_cast<int*>(fw + o_dec);
-      fa.spin_limit = 1LL << 24;
+      fa.spin_limit = o.wait_polls > 0 ? (long long)o.wait_polls : 1LL << 24;
+      fa.slow_block = o.slow_block;
+      fa.slow_ns = o.slow_ns;
       int occ = 0;
       MS_CUDA(g, res_flow_max_clusters(shape.variant, shape.cluster, shape.smem, &occ));
       const int fslots = std::max(1, std::min(occ, ntasks));

@@ -133,6 +133,57 @@ __device__ __forceinline__ float cluster_sum_f32(float v, float* slots, float* w
   return acc;
 }
 
+// The two halves of cl_barrier(), for work in between: every thread of the
+// cluster arrives (release: its earlier global and shared writes, DSMEM
+// stores included, become visible to the cluster) and later waits (acquire)
+// until every thread has arrived.  Each thread alternates arrive and wait;
+// no other cluster barrier may sit between them.
+__device__ __forceinline__ void cl_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cl_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+
+// cluster_sum_f32 for two values at once (one CTA barrier, one cluster
+// barrier): a and b are replaced by their cluster-wide totals, bit-identical
+// in every thread.  Same slot rules as cluster_sum_f32, for both slot arrays.
+template <int NT>
+__device__ __forceinline__ void cluster_sum2_f32(float& a, float& b, float* slots_a, float* slots_b, float* wsum_a,
+                                                 float* wsum_b, unsigned rank, unsigned csize) {
+  constexpr int NW = NT / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if (lane == 0) {
+    wsum_a[warp] = a;
+    wsum_b[warp] = b;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    float ta = lane < NW ? wsum_a[lane] : 0.f;
+    float tb = lane < NW ? wsum_b[lane] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ta += __shfl_xor_sync(0xffffffffu, ta, o);
+      tb += __shfl_xor_sync(0xffffffffu, tb, o);
+    }
+    if (lane < (int)csize) {
+      st_cluster_f32(&slots_a[rank], (unsigned)lane, ta);
+      st_cluster_f32(&slots_b[rank], (unsigned)lane, tb);
+    }
+  }
+  cl_barrier();
+  float xa = lane < (int)csize ? slots_a[lane] : 0.f;
+  float xb = lane < (int)csize ? slots_b[lane] : 0.f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    xa += __shfl_xor_sync(0xffffffffu, xa, o);
+    xb += __shfl_xor_sync(0xffffffffu, xb, o);
+  }
+  a = xa;
+  b = xb;
+}
+
 // Reduction slots of an FP32 CG iteration (resident and vectorised streaming
 // engines): CTA totals, one per rank, and this CTA's warp totals, for the
 // iteration's two sums (see cluster_sum_f32).

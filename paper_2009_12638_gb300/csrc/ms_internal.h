@@ -141,7 +141,8 @@ struct FlowArgs {
   int* res_cnt;                  // [outer_maxit + 2 - k0] residuals counted per sweep
   int* done_rel;                 // [ntasks] sweeps completed since k0
   int* decided_rel;              // last sweep (relative) whose stop decision is made, -1 before any
-  long long spin_limit;          // polls before a wait gives up (kErrTimeout)
+  long long spin_limit;          // polls before a wait gives up (kErrTimeout), summed over the launch
+  int slow_block, slow_ns;       // resilience test: this block sleeps slow_ns per task (-1 = none)
 };
 
 // Asynchronous persistent solve (see ms_async.cu).  Task t = (block, rhs) is

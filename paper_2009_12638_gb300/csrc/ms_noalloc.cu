@@ -1,19 +1,21 @@
 // ms_noalloc.cu -- ms_residual_noalloc: the true relative residual of
 // ms_residual, computed without allocating any device memory.
 //
-// Who needs it: callers that cannot call cudaMalloc at this point -- a code
-// path that runs while a CUDA graph is being captured (an allocation there
-// breaks or invalidates the capture), a latency-critical loop in which
-// cudaMalloc's implicit device synchronisation is not acceptable, or an
-// application whose device memory is entirely owned by its own pool
-// allocator.  ms_residual itself grows a per-handle workspace with
+// Who needs it: callers that cannot call cudaMalloc at this point -- a
+// latency-critical loop in which cudaMalloc's implicit device
+// synchronisation is not acceptable, or an application whose device memory
+// is entirely owned by its own pool allocator and may not be allocated
+// behind its back.  ms_residual itself grows a per-handle workspace with
 // cudaMalloc on first use; this variant never does.
 //
 // Its scratch (per-CTA partial sums) is the file-scope device array below,
 // of fixed size.  Host code must not hand the symbol itself to a kernel (on
 // the host it is only a stand-in, not a device address): the address is
 // resolved once per device with cudaGetSymbolAddress, with that device
-// current, on the first call made on that device.  Every call on a device
+// current, on the first call made on that device (make that call before any
+// stream capture on the device), and cached; after cudaDeviceReset the cached
+// address may be stale, so the function must not be used again on that
+// device in the same process.  Every call on a device
 // shares the one array: calls whose kernels overlap on the GPU (different
 // streams, no ordering between them) race on it.  Each call writes every
 // partial it later reads, so nothing needs clearing between calls.

@@ -9,7 +9,7 @@
 
 namespace ms {
 
-static_assert(kNumResVariants == 16, "one case per variant row");
+static_assert(kNumResVariants == 21, "one case per variant row");
 
 static cudaError_t res_fn(int variant, int cluster, size_t smem_bytes, void** fn, int am = 0) {
   switch (variant) {
@@ -29,6 +29,11 @@ static cudaError_t res_fn(int variant, int cluster, size_t smem_bytes, void** fn
     case 13: return res_prep<13>(cluster, smem_bytes, fn, am);
     case 14: return res_prep<14>(cluster, smem_bytes, fn, am);
     case 15: return res_prep<15>(cluster, smem_bytes, fn, am);
+    case 16: return res_prep<16>(cluster, smem_bytes, fn, am);
+    case 17: return res_prep<17>(cluster, smem_bytes, fn, am);
+    case 18: return res_prep<18>(cluster, smem_bytes, fn, am);
+    case 19: return res_prep<19>(cluster, smem_bytes, fn, am);
+    case 20: return res_prep<20>(cluster, smem_bytes, fn, am);
     default: return cudaErrorInvalidValue;
   }
 }

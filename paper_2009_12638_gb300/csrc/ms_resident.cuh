@@ -136,16 +136,158 @@ __device__ __forceinline__ float4* d_slot(float* sp, const ResGeo& g, int z, int
   return reinterpret_cast<float4*>(sp + (long long)(ZS + 4) * g.ps) + (long long)z * g.nstrips + st;
 }
 
+// Single-reduction CG (Chronopoulos and Gear's rearrangement of the same
+// method: identical iterates in exact arithmetic, one cluster reduction per
+// iteration instead of two).  With w = A r, gamma = r.r and delta = w.r
+// summed together, beta = gamma_new / gamma, eta = p.A p = delta - beta
+// gamma_new / alpha, alpha = gamma_new / eta, and the recurrences
+//   p = r + beta p,  s = w + beta s  (s = A p),  d += alpha p,  r -= alpha s.
+// Layout: r lives in the shared-memory plane stack (planes 0 and nzs+1 are the
+// neighbour CTAs' boundary planes of r), p, s and w in registers, d in shared
+// memory (compact planes, as the DS layouts).  Per iteration: one update pass
+// (writes r and pushes its first/last plane into the neighbours' halo planes),
+// then the stencil w = A r: its interior planes run between the arrive and
+// the wait of a split cluster barrier that publishes the pushed planes, its
+// two boundary planes after the wait; then the one reduction of (r.r, w.r).
+// The stop rules are those of the two-reduction loop: the cap after m
+// updates, ||r_m|| <= inner_rtol ||r_0|| after each update, eta <= 0 before it.
+// On entry r4 holds r, the residual phase has pushed the neighbours' boundary
+// planes of r into the r-halo planes (visible after its cluster barrier), and
+// shared memory is otherwise zero.  Returns m; d is in shared memory.
+template <int NT, int KC, int ZS>
+__device__ int resident_cg_one_reduction(float4 (&r4)[KC][ZS], const ResGeo& g, const Strips<KC>& s, float* sp,
+                                         float gamma0, float inner_rtol, int inner_maxit, ResRed& rr, unsigned rank,
+                                         unsigned csize) {
+  const float* rh_lo = sp + (long long)(ZS + 2) * g.ps;  // residual phase: neighbour below's top plane of r
+  const float* rh_hi = rh_lo + g.ps;                     // neighbour above's bottom plane of r
+  const bool has_lo = rank > 0, has_hi = rank + 1 < csize;
+  if (!(gamma0 > 0.f) || inner_maxit <= 0) return 0;
+  // plane count of the slab below (its top halo plane is its plane nzs + 1)
+  const int nzs_lo = has_lo ? (int)(((long long)g.bz * rank) / csize) - (int)(((long long)g.bz * (rank - 1)) / csize)
+                            : 0;
+  auto plane = [&](int z) { return sp + (long long)z * g.ps; };
+  auto axpy4 = [](float a, float4 x, float4 y) {  // a x + y, per component
+    return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+  };
+  // r into the plane stack: own planes from registers, halo planes from the residual's pushes
+#pragma unroll
+  for (int k = 0; k < KC; ++k) {
+    if (!s.msk[k]) continue;
+    const int o = s.off[k];
+#pragma unroll
+    for (int z = 0; z < ZS; ++z) {
+      if (z >= g.nzs) break;
+      sts4(plane(z + 1) + o, r4[k][z]);
+    }
+    if (has_lo) sts4(plane(0) + o, lds4(rh_lo + o));
+    if (has_hi) sts4(plane(g.nzs + 1) + o, lds4(rh_hi + o));
+  }
+  __syncthreads();
+  float4(&p4)[KC][ZS] = r4;  // p = r at the first update (beta = 0)
+  float4 s4[KC][ZS], w4[KC][ZS];
+  // w = A r on own plane z (stack planes z, z+1, z+2), with the r.r and w.r terms
+  auto stencil_plane = [&](int k, int z, float& gl, float& dl) {
+    const float* cp = plane(z + 1) + s.off[k];
+    const float4 c = lds4(cp);
+    const float4 w = mask4(stencil4(cp, g.rp, c, lds4(cp - g.ps), lds4(cp + g.ps), s.nb[k] & 1u, s.nb[k] & 2u),
+                           s.msk[k]);
+    w4[k][z] = w;
+    gl += dot4(c, c);
+    dl += dot4(w, c);
+  };
+  // prologue: w = A r, gamma = r.r, delta = w.r (every plane: the halos are in place)
+  float gam = 0.f, del = 0.f;
+#pragma unroll
+  for (int k = 0; k < KC; ++k) {
+#pragma unroll
+    for (int z = 0; z < ZS; ++z) {
+      if (z >= g.nzs) break;
+      stencil_plane(k, z, gam, del);
+    }
+  }
+  cluster_sum2_f32<NT>(gam, del, rr.eta, rr.gam, rr.weta, rr.wgam, rank, csize);
+  if (!(del > 0.f)) return 0;  // eta = p.A p with p = r
+#pragma unroll
+  for (int k = 0; k < KC; ++k)
+#pragma unroll
+    for (int z = 0; z < ZS; ++z) s4[k][z] = w4[k][z];  // s = A p = w (beta = 0 below)
+  const float stop = inner_rtol * sqrtf(gamma0);
+  float gamma = gam, alpha = gam / del, beta = 0.f;
+  int m = 0;
+  for (;;) {
+    // ---------------- update: p, s, d, r; r's boundary planes to the neighbours
+    const bool last = m + 1 >= inner_maxit;  // after this update nothing reads r again
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+      if (!s.msk[k]) continue;
+#pragma unroll
+      for (int z = 0; z < ZS; ++z) {
+        if (z >= g.nzs) break;
+        float* rp = plane(z + 1) + s.off[k];
+        const float4 r = lds4(rp);
+        const float4 p = axpy4(beta, p4[k][z], r);
+        p4[k][z] = p;
+        float4* dp = d_slot<NT, KC, ZS, true>(sp, g, z, s.st[k]);
+        const float4 d = m == 0 ? make_float4(0.f, 0.f, 0.f, 0.f) : *dp;
+        *dp = axpy4(alpha, p, d);
+        if (last) continue;
+        const float4 sv = axpy4(beta, s4[k][z], w4[k][z]);
+        s4[k][z] = sv;
+        const float4 rn = axpy4(-alpha, sv, r);
+        sts4(rp, rn);
+        if (z == 0 && has_lo) st_cluster_v4(plane(nzs_lo + 1) + s.off[k], rank - 1, rn);
+        if (z == g.nzs - 1 && has_hi) st_cluster_v4(plane(0) + s.off[k], rank + 1, rn);
+      }
+    }
+    m += 1;
+    if (last) break;
+    // ---------------- w = A r: interior planes while the halo planes travel
+    cl_arrive();
+    __syncthreads();
+    float gl = 0.f, dl = 0.f;
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+#pragma unroll
+      for (int z = 1; z < ZS - 1; ++z) {
+        if (z >= g.nzs - 1) break;
+        stencil_plane(k, z, gl, dl);
+      }
+    }
+    cl_wait();
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+#pragma unroll
+      for (int z = 0; z < ZS; ++z) {  // planes 0 and nzs - 1 (compile-time indices into w4)
+        if (z >= g.nzs) break;
+        if (z == 0 || z == g.nzs - 1) stencil_plane(k, z, gl, dl);
+      }
+    }
+    cluster_sum2_f32<NT>(gl, dl, rr.eta, rr.gam, rr.weta, rr.wgam, rank, csize);
+    if (sqrtf(gl) <= stop) break;
+    beta = gl / gamma;
+    const float eta = dl - beta * gl / alpha;
+    if (!(eta > 0.f)) break;  // curvature breakdown or NaN: keep d from earlier steps
+    alpha = gl / eta;
+    gamma = gl;
+  }
+  // callers read d (own strips) and then clear shared memory for the next task:
+  // every remote store of this solve precedes a cluster barrier that every CTA has
+  // passed (the last update pushes nothing), and no thread may clear while another
+  // still reads r
+  __syncthreads();
+  return m;
+}
+
 // QR: q = A_ii p of pass A stays in registers for pass B (no second stencil),
 // and the update d += alpha p moves to the next pass C, which reads p_old
 // anyway (the last one runs after the loop).  The FMAs and their order are
-// those of the QR = false path, so both give bit-identical results; QR costs
+// those of the QR = 0 path, so both give bit-identical results; QR costs
 // 4 registers per strip-plane and saves pass B's shared-memory reads.
 template <int NT, int KC, int ZS, bool DS, bool QR>
-__device__ int resident_cg(float4 (&r4)[KC][ZS], float4 (&d4)[DS ? 1 : KC][DS ? 1 : ZS], const ResGeo& g,
-                           const Strips<KC>& s,
-                           float* sp, float gamma0, float inner_rtol, int inner_maxit, ResRed& rr, unsigned rank,
-                           unsigned csize) {
+__device__ int resident_cg_two_reductions(float4 (&r4)[KC][ZS], float4 (&d4)[DS ? 1 : KC][DS ? 1 : ZS],
+                                          const ResGeo& g, const Strips<KC>& s, float* sp, float gamma0,
+                                          float inner_rtol, int inner_maxit, ResRed& rr, unsigned rank,
+                                          unsigned csize) {
   float* rh_lo = sp + (long long)(ZS + 2) * g.ps;  // neighbour below's top plane of r
   float* rh_hi = rh_lo + g.ps;                     // neighbour above's bottom plane of r
   float* p_lo = sp;                                // p halo plane below (plane 0)
@@ -282,6 +424,23 @@ __device__ int resident_cg(float4 (&r4)[KC][ZS], float4 (&d4)[DS ? 1 : KC][DS ? 
     __syncthreads();
   }
   return m;
+}
+
+// The inner CG of one task on the resident state: QR = 0 two stencils per
+// iteration, QR = 1 q = A p kept in registers (bit-identical to QR = 0),
+// QR = 2 the single-reduction CG (d in shared memory: DS = true).
+template <int NT, int KC, int ZS, bool DS, int QR>
+__device__ __forceinline__ int resident_cg(float4 (&r4)[KC][ZS], float4 (&d4)[DS ? 1 : KC][DS ? 1 : ZS],
+                                           const ResGeo& g, const Strips<KC>& s, float* sp, float gamma0,
+                                           float inner_rtol, int inner_maxit, ResRed& rr, unsigned rank,
+                                           unsigned csize) {
+  if constexpr (QR == 2) {
+    static_assert(DS, "the single-reduction CG keeps d in shared memory");
+    return resident_cg_one_reduction<NT, KC, ZS>(r4, g, s, sp, gamma0, inner_rtol, inner_maxit, rr, rank, csize);
+  } else {
+    return resident_cg_two_reductions<NT, KC, ZS, DS, QR == 1>(r4, d4, g, s, sp, gamma0, inner_rtol, inner_maxit,
+                                                                rr, rank, csize);
+  }
 }
 
 }  // namespace ms

@@ -89,7 +89,7 @@ __device__ __forceinline__ void zero_smem(float4* p, int n4) {
   for (int i = threadIdx.x; i < n4; i += NT) p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-template <int NT, int KC, int ZS, bool DS, bool QR>
+template <int NT, int KC, int ZS, bool DS, int QR>
 __global__ void __launch_bounds__(NT, 1) res_sweep_kernel(const SweepArgs a, int smem_f4) {
   extern __shared__ float4 dyn4[];
   float* sp = reinterpret_cast<float*>(dyn4);
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(NT, 1) res_sweep_kernel(const SweepArgs a, int
 // Asynchronous outer iteration with the on-chip inner CG (protocol in
 // ms_async.cuh): halo refresh, residual through the halo cache, resident CG,
 // in-place update fused with face publication, stale-estimate monitor.
-template <int NT, int KC, int ZS, bool DS, bool QR>
+template <int NT, int KC, int ZS, bool DS, int QR>
 __global__ void __launch_bounds__(NT, 1) res_async_kernel(const AsyncArgs a, int smem_f4) {
   extern __shared__ float4 dyn4[];
   float* sp = reinterpret_cast<float*>(dyn4);
@@ -303,16 +303,19 @@ __device__ __forceinline__ void st_rel_s32(int* p, int v) {
   asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Bounded wait until *p >= v (thread 0 of rank 0 only).  Gives up after
-// `limit` polls; backs off with __nanosleep.
-__device__ __forceinline__ bool flow_wait_ge(const int* p, int v, long long& limit) {
+// Bounded wait until *p >= v (warp 0 of rank 0 only).  Returns 1 when the
+// flag is reached, -1 when *abort is set meanwhile (another cluster ended the
+// launch: leave without an error of our own), 0 when `limit` polls (summed
+// over the launch) are spent.  Backs off with __nanosleep.
+__device__ __forceinline__ int flow_wait_ge(const int* p, int v, const int* abort, long long& limit) {
   unsigned ns = 32;
   while (ld_acq_s32(p) < v) {
-    if (--limit < 0) return false;
+    if (ld_acq_s32(abort)) return -1;
+    if (--limit < 0) return 0;
     __nanosleep(ns);
     ns = ns < 1024 ? 2 * ns : 1024;
   }
-  return true;
+  return 1;
 }
 
 // Stop decision for sweep k (relative kr) -- the one-CTA check kernel's work,
@@ -376,7 +379,7 @@ __device__ __forceinline__ int flow_nbr(const FlowArgs& fa, const Task& tk, int 
   return fa.task_of[(long long)tk.rhs * fa.nblocks + bi + fa.px * (bj + fa.py * bk)];
 }
 
-template <int NT, int KC, int ZS, bool DS, bool QR>
+template <int NT, int KC, int ZS, bool DS, int QR>
 __global__ void __launch_bounds__(NT, 1) res_flow_kernel(const FlowArgs fa, int smem_f4) {
   extern __shared__ float4 dyn4[];
   float* sp = reinterpret_cast<float*>(dyn4);
@@ -402,14 +405,17 @@ __global__ void __launch_bounds__(NT, 1) res_flow_kernel(const FlowArgs fa, int 
         t = (int)(j % (unsigned long long)a.ntasks);
         if (kr > last_rel || ld_acq_s32(a.all_done)) {
           cmd = 2;
-        } else if (kr > 0 && !flow_wait_ge(fa.decided_rel, kr - 1, limit)) {
-          atomicOr(a.err, kErrTimeout);
-          st_rel_s32(const_cast<int*>(a.all_done), 1);
-          cmd = 2;
-        } else if (ld_acq_s32(a.all_done)) {
-          cmd = 2;
-        } else if (a.rhs_state[a.tasks[t].rhs] != kActive) {
-          cmd = 1;
+        } else {
+          const int w = kr > 0 ? flow_wait_ge(fa.decided_rel, kr - 1, a.all_done, limit) : 1;
+          if (w == 0) {
+            atomicOr(a.err, kErrTimeout);
+            st_rel_s32(const_cast<int*>(a.all_done), 1);
+            cmd = 2;
+          } else if (w < 0 || ld_acq_s32(a.all_done)) {
+            cmd = 2;
+          } else if (a.rhs_state[a.tasks[t].rhs] != kActive) {
+            cmd = 1;
+          }
         }
       }
       cmd = __shfl_sync(0xffffffffu, cmd, 0);
@@ -417,13 +423,15 @@ __global__ void __launch_bounds__(NT, 1) res_flow_kernel(const FlowArgs fa, int 
       t = __shfl_sync(0xffffffffu, t, 0);
       if (cmd == 0) {
         // lanes 0..6 wait for the block itself and its six neighbours to finish sweep kr-1
-        bool ok = true;
+        int w = 1;
         if (lane < 7) {
           const int who = lane == 0 ? t : flow_nbr(fa, a.tasks[t], lane - 1);
-          if (who >= 0) ok = flow_wait_ge(fa.done_rel + who, kr, limit);
+          if (who >= 0) w = flow_wait_ge(fa.done_rel + who, kr, a.all_done, limit);
         }
-        if (!__all_sync(0xffffffffu, ok)) {
-          if (lane == 0) {
+        if (!__all_sync(0xffffffffu, w > 0)) {
+          // a lane that ran out of polls ends the launch with kErrTimeout; a lane
+          // that saw another cluster end it leaves quietly
+          if (!__all_sync(0xffffffffu, w != 0) && lane == 0) {
             atomicOr(a.err, kErrTimeout);
             st_rel_s32(const_cast<int*>(a.all_done), 1);
           }
@@ -453,6 +461,8 @@ __global__ void __launch_bounds__(NT, 1) res_flow_kernel(const FlowArgs fa, int 
       continue;
     }
     const int k = fa.k0 + kr;
+    if (fa.slow_block == a.tasks[t].block && fa.slow_ns > 0 && rank == 0 && tid == 0)
+      __nanosleep((unsigned)min(fa.slow_ns, 1000000));
     // x is written by other clusters during this launch, so it is never read through the
     // non-coherent read-only path (no const __restrict__ on it); ordinary loads see the
     // producers' writes through the acquire chain (done flag ld.acquire.gpu by rank 0 ->
@@ -536,7 +546,7 @@ __global__ void __launch_bounds__(NT, 1) res_flow_kernel(const FlowArgs fa, int 
   }
 }
 
-template <int NT, int KC, int ZS, bool DS, bool QR>
+template <int NT, int KC, int ZS, bool DS, int QR>
 inline cudaError_t prep_res(int cluster, size_t smem_bytes, void** fn, int kind) {
   void (*kern)(const SweepArgs, int) = res_sweep_kernel<NT, KC, ZS, DS, QR>;
   void (*akern)(const AsyncArgs, int) = res_async_kernel<NT, KC, ZS, DS, QR>;
@@ -574,7 +584,7 @@ inline cudaError_t prep_res(int cluster, size_t smem_bytes, void** fn, int kind)
 template <int V>
 cudaError_t res_prep(int cluster, size_t smem_bytes, void** fn, int kind) {
   constexpr ResVariant r = kResVariants[V];
-  return prep_res<r.nt, r.kc, r.zs, r.ds != 0, r.qr != 0>(cluster, smem_bytes, fn, kind);
+  return prep_res<r.nt, r.kc, r.zs, r.ds != 0, r.qr>(cluster, smem_bytes, fn, kind);
 }
 
 }  // namespace ms

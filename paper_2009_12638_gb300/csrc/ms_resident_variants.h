@@ -9,15 +9,18 @@ namespace ms {
 
 // ---------------------------------------------------------------- variants
 // (NT threads, KC strips per thread, ZS planes per CTA at most, d in shared
-// memory, q kept in registers between passes A and B)
+// memory, qr: 0 = two stencils per CG iteration, 1 = q = A p kept in
+// registers between passes A and B, 2 = the single-reduction CG, which keeps
+// p, s = A p and w = A r in registers and needs d in shared memory)
 struct ResVariant {
   int nt, kc, zs, ds, qr;
 };
 constexpr ResVariant kResVariants[] = {
-    {512, 2, 4, 0, 0},  {512, 1, 8, 0, 0},  {256, 2, 4, 0, 0},  {256, 1, 8, 0, 0}, {512, 4, 2, 0, 0},
-    {1024, 1, 4, 1, 0}, {1024, 2, 2, 1, 0}, {1024, 1, 8, 1, 0}, {512, 2, 4, 1, 0}, {512, 2, 4, 0, 1},
-    {512, 1, 8, 0, 1},  {256, 2, 4, 0, 1},  {256, 1, 8, 0, 1},  {512, 2, 4, 1, 1}, {512, 4, 2, 0, 1},
-    {1024, 1, 4, 1, 1}};
+    {512, 2, 4, 0, 0},  {512, 1, 8, 0, 0},  {256, 2, 4, 0, 0},  {256, 1, 8, 0, 0},  {512, 4, 2, 0, 0},
+    {1024, 1, 4, 1, 0}, {1024, 2, 2, 1, 0}, {1024, 1, 8, 1, 0}, {512, 2, 4, 1, 0},  {512, 2, 4, 0, 1},
+    {512, 1, 8, 0, 1},  {256, 2, 4, 0, 1},  {256, 1, 8, 0, 1},  {512, 2, 4, 1, 1},  {512, 4, 2, 0, 1},
+    {1024, 1, 4, 1, 1}, {512, 2, 4, 1, 2},  {256, 1, 8, 1, 2},  {256, 2, 4, 1, 2},  {512, 1, 8, 1, 2},
+    {1024, 1, 4, 1, 2}};
 constexpr int kNumResVariants = sizeof(kResVariants) / sizeof(kResVariants[0]);
 
 

@@ -74,7 +74,12 @@ static void list_resident(Tuner& t, int mode, const std::vector<Task>& tasks, lo
       // the tuner) holds more state: with q in registers it spills at 512 and
       // 1024 threads (measured 5% slower at 256^3), so there QR only pays at
       // <= 256 threads (measured 27% faster at 128^3)
-      const double qr_factor = !qr ? 1.0 : (mode == 1 && nt > 256 ? 1.05 : 0.85);
+      // The single-reduction CG (qr 2) halves the cluster sums per iteration but
+      // moves d to shared memory and reads more of it per iteration: measured
+      // 4.02 vs 3.01 ms per 256^3 sweep against the best q-in-registers row, so
+      // it ranks behind the two-reduction rows and is kept where it measures faster.
+      const double qr_factor =
+          qr == 2 ? 1.1 : (!qr ? 1.0 : (mode == 1 && nt > 256 ? 1.05 : 0.85));
       r.est = rounds * ((double)maxpts / c) * (1.0 + 0.02 * c) * qr_factor;
       out->push_back(r);
     }

@@ -47,9 +47,10 @@ def test_ctypes_structs_match_c_layout(tmp_path):
 #include <stddef.h>
 #include "ms.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(ms_opts), offsetof(ms_opts, outer_tol), offsetof(ms_opts, res_hist),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(ms_opts), offsetof(ms_opts, outer_tol), offsetof(ms_opts, res_hist),
          offsetof(ms_opts, slow_ns), offsetof(ms_opts, time_limit_ms), offsetof(ms_opts, variant),
-         offsetof(ms_opts, inner_adapt), offsetof(ms_opts, overlap), offsetof(ms_opts, gmres_restart));
+         offsetof(ms_opts, inner_adapt), offsetof(ms_opts, overlap), offsetof(ms_opts, gmres_restart),
+         offsetof(ms_opts, wait_polls));
   printf("%zu %zu %zu %zu %zu %zu\n", sizeof(ms_stats), offsetof(ms_stats, lups), offsetof(ms_stats, per_rhs_rel),
          offsetof(ms_stats, slots), offsetof(ms_stats, variant), offsetof(ms_stats, inner_rtol_final));
   return 0;
@@ -61,7 +62,8 @@ int main(void) {
     O, S = _lib.Opts, _lib.Stats
     assert [int(v) for v in a.split()] == [ctypes.sizeof(O), O.outer_tol.offset, O.res_hist.offset,
                                           O.slow_ns.offset, O.time_limit_ms.offset, O.variant.offset,
-                                          O.inner_adapt.offset, O.overlap.offset, O.gmres_restart.offset]
+                                          O.inner_adapt.offset, O.overlap.offset, O.gmres_restart.offset,
+                                          O.wait_polls.offset]
     assert [int(v) for v in b.split()] == [ctypes.sizeof(S), S.lups.offset, S.per_rhs_rel.offset, S.slots.offset,
                                           S.variant.offset, S.inner_rtol_final.offset]
 
@@ -73,6 +75,7 @@ def test_default_opts(lib):
     assert o.slow_block == -1 and o.use_graph == 1
     assert o.variant == -1 and o.inner_adapt == 0 and o.overlap == 0
     assert o.inner_method == 0 and o.gmres_restart == 10
+    assert o.wait_polls == 0
 
 
 def test_resident_variant_table(lib):
@@ -81,18 +84,21 @@ def test_resident_variant_table(lib):
     assert len(rows) >= 2
     for r in rows:
         assert r["threads"] in (256, 512, 1024) and r["strips"] >= 1 and r["planes"] >= 1
-        assert r["d_smem"] in (0, 1) and r["q_regs"] in (0, 1)
-    # every layout that keeps q in registers has a twin that does not (the
-    # GPU tests compare the two bit for bit)
+        assert r["d_smem"] in (0, 1) and r["q_regs"] in (0, 1) and r["one_reduction"] in (0, 1)
+        # the single-reduction CG keeps d in shared memory and has no separate q
+        assert not r["one_reduction"] or (r["d_smem"] and not r["q_regs"])
+    # every two-reduction layout that keeps q in registers has a twin that does
+    # not (the GPU tests compare the two bit for bit)
     key = lambda r: (r["threads"], r["strips"], r["planes"], r["d_smem"])  # noqa: E731
-    plain = {key(r) for r in rows if not r["q_regs"]}
+    plain = {key(r) for r in rows if not r["q_regs"] and not r["one_reduction"]}
     assert all(key(r) in plain for r in rows if r["q_regs"])
+    assert any(r["one_reduction"] for r in rows)
     n = ctypes.c_int(0)
     t = ctypes.c_int(0)
-    assert lib.ms_resident_variant(len(rows), ctypes.byref(n), ctypes.byref(t), None, None, None, None) == \
+    assert lib.ms_resident_variant(len(rows), ctypes.byref(n), ctypes.byref(t), None, None, None, None, None) == \
         _lib.MS_ERR_ARG
     assert n.value == len(rows)
-    assert lib.ms_resident_variant(-1, None, None, None, None, None, None) == _lib.MS_ERR_ARG
+    assert lib.ms_resident_variant(-1, None, None, None, None, None, None, None) == _lib.MS_ERR_ARG
 
 
 def test_boundary_size(lib):

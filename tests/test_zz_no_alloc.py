@@ -1,6 +1,7 @@
 """ms_residual_noalloc: the residual entry point for callers that cannot
-allocate device memory at the point of the call (inside a graph capture, in a
-latency-critical loop, or with all memory owned by their own pool).  It must
+allocate device memory at the point of the call (in a latency-critical loop
+that cannot absorb cudaMalloc's implicit synchronisation, or with all device
+memory owned by their own pool allocator).  It must
 give the same numbers as ms_residual, call after call, although its scratch
 is one fixed device array shared by every call.
 
