@@ -386,13 +386,15 @@ __global__ void __launch_bounds__(NT, 1) res_flow_kernel(const FlowArgs fa, int 
   __shared__ RedSmem red;
   __shared__ ResRed rred;
   __shared__ int bc[2][4];  // cmd (0 run, 1 skip, 2 leave), relative sweep, task
+  // poll budgets of the bounded waits, one per lane of warp 0 of rank 0 (kept in
+  // shared memory: no register stays live across the inner CG for them)
+  __shared__ long long wait_budget[32];
   const SweepArgs& a = fa.s;
   const unsigned rank = cl_rank(), csize = cl_size();
   const int tid = threadIdx.x;
   const Geo G = a.g;
   const long long nxy = (long long)G.nx * G.ny;
-  const int last_rel = a.outer_maxit - fa.k0;  // the residual-only sweep
-  long long limit = fa.spin_limit;             // warp 0 of rank 0 only
+  if (tid < 32) wait_budget[tid] = fa.spin_limit;
   zero_smem<NT>(dyn4, smem_f4);
   int par = 0;
   for (;; par ^= 1) {
@@ -403,10 +405,10 @@ __global__ void __launch_bounds__(NT, 1) res_flow_kernel(const FlowArgs fa, int 
         const unsigned long long j = atomicAdd(fa.ticket, 1ull);
         kr = (int)(j / (unsigned long long)a.ntasks);
         t = (int)(j % (unsigned long long)a.ntasks);
-        if (kr > last_rel || ld_acq_s32(a.all_done)) {
+        if (kr > a.outer_maxit - fa.k0 || ld_acq_s32(a.all_done)) {  // past the residual-only sweep
           cmd = 2;
         } else {
-          const int w = kr > 0 ? flow_wait_ge(fa.decided_rel, kr - 1, a.all_done, limit) : 1;
+          const int w = kr > 0 ? flow_wait_ge(fa.decided_rel, kr - 1, a.all_done, wait_budget[0]) : 1;
           if (w == 0) {
             atomicOr(a.err, kErrTimeout);
             st_rel_s32(const_cast<int*>(a.all_done), 1);
@@ -426,7 +428,7 @@ __global__ void __launch_bounds__(NT, 1) res_flow_kernel(const FlowArgs fa, int 
         int w = 1;
         if (lane < 7) {
           const int who = lane == 0 ? t : flow_nbr(fa, a.tasks[t], lane - 1);
-          if (who >= 0) w = flow_wait_ge(fa.done_rel + who, kr, a.all_done, limit);
+          if (who >= 0) w = flow_wait_ge(fa.done_rel + who, kr, a.all_done, wait_budget[lane]);
         }
         if (!__all_sync(0xffffffffu, w > 0)) {
           // a lane that ran out of polls ends the launch with kErrTimeout; a lane
@@ -502,7 +504,7 @@ __global__ void __launch_bounds__(NT, 1) res_flow_kernel(const FlowArgs fa, int 
       }
       if (__shfl_sync(0xffffffffu, last, 0)) flow_decide(fa, kr);
     }
-    if (kr == last_rel) {  // residual only: nothing more to do for this sweep
+    if (kr == a.outer_maxit - fa.k0) {  // the residual-only sweep: nothing more to do for it
       zero_smem<NT>(dyn4, smem_f4);
       if (rank == 0 && tid == 0) st_rel_s32(fa.done_rel + t, kr + 1);
       continue;

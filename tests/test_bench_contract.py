@@ -38,13 +38,13 @@ def test_traffic_follows_the_kernel_source_hash(tmp_path, monkeypatch):
     f = tmp_path / "traffic.json"
     f.write_text(json.dumps(rec))
     monkeypatch.setattr(bench, "TRAFFIC_FILE", str(f))
-    assert bench.measured_traffic("res_sweep_kernel") == (12345.0, rec["source_hash"])
-    assert bench.measured_traffic("strip_sweep_kernel")[0] is None  # another kernel
+    assert bench.measured_record("res_sweep_kernel")["dram_bytes_per_launch"] == 12345
+    assert bench.measured_record("strip_sweep_kernel") is None  # another kernel
     rec["source_hash"] = "0" * 16  # sources changed since the capture
     f.write_text(json.dumps(rec))
-    assert bench.measured_traffic("res_sweep_kernel") == (None, "0" * 16)
+    assert bench.measured_record("res_sweep_kernel") is None
     monkeypatch.setattr(bench, "TRAFFIC_FILE", str(tmp_path / "missing.json"))
-    assert bench.measured_traffic("res_sweep_kernel") == (None, None)
+    assert bench.measured_record("res_sweep_kernel") is None
 
 
 def test_kernel_source_hash_is_stable_and_covers_the_resident_sources():

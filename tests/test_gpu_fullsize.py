@@ -88,6 +88,11 @@ def test_laplace512_first_sweep_sampled_rhs():
 
 
 def test_adjoint128_central_fd():
+    """The 128^3 adjoint workload: gradients of L = 0.5 ||u - u_t||^2 with
+    respect to f and the Dirichlet data, from the adjoint solve, against central
+    differences along 64 Gaussian probes.  L is quadratic in (f, g), so central
+    differences are exact up to rounding and solve error (both solves to 1e-12).
+    The 128 perturbed solves run as batched multi-rhs solves, 32 rhs each."""
     cfg = inputs.make_config("adjoint128")
     n = cfg["nx"]
     g = grid_for(cfg)
@@ -99,23 +104,32 @@ def test_adjoint128_central_fd():
     gb = g0.clone().requires_grad_(True)
     u = MsSolve.apply(f, gb, g, opts)
     (0.5 * ((u - target) ** 2).sum()).backward()
-    nprobe = 6
+    nprobe = cfg["nprobes"]
+    assert nprobe == 64
     vf = inputs.gaussian_probes((1, n, n, n), nprobe, cfg["probe_seed"])
     vg = inputs.gaussian_probes((1, g.nbnd), nprobe, cfg["probe_seed"] + 1)
     theta = float(torch.linalg.vector_norm(g0))
-    for i in range(nprobe):
-        v_f = torch.from_numpy(vf[i]).cuda()
-        v_g = torch.from_numpy(vg[i]).cuda()
-        eps = 1e-2 * theta / float(torch.sqrt((v_f ** 2).sum() + (v_g ** 2).sum()))
-
-        def L(s):
-            uu, st = g.solve(f=f0 + s * v_f, bnd=g0 + s * v_g, **opts)
-            assert st.status == 0
-            return 0.5 * float(((uu - target) ** 2).sum())
-
-        fd = (L(eps) - L(-eps)) / (2 * eps)
-        ad = float((f.grad * v_f).sum() + (gb.grad * v_g).sum())
-        assert abs(ad - fd) <= 1e-6 * abs(fd), (i, ad, fd)
+    per = 16  # probes per batched solve (2 rhs each: +eps and -eps)
+    gbatch = Grid(n, n, n, 2 * per).partition(4, 4, 4, cfg["cx"], cfg["cy"], cfg["cz"])
+    errs = []
+    for start in range(0, nprobe, per):
+        ids = range(start, start + per)
+        v_f = torch.from_numpy(np.concatenate([vf[i] for i in ids])).cuda()  # (per, n, n, n)
+        v_g = torch.from_numpy(np.concatenate([vg[i] for i in ids])).cuda()  # (per, nbnd)
+        eps = 1e-2 * theta / torch.sqrt((v_f ** 2).sum(dim=(1, 2, 3)) + (v_g ** 2).sum(dim=1))  # (per,)
+        sign = torch.tensor([1.0, -1.0], dtype=torch.float64, device="cuda")
+        se = (sign[None, :] * eps[:, None]).reshape(-1)  # rhs 2i: +eps_i, 2i+1: -eps_i
+        fb = f0 + se[:, None, None, None] * v_f.repeat_interleave(2, dim=0)
+        bb = g0 + se[:, None] * v_g.repeat_interleave(2, dim=0)
+        uu, st = gbatch.solve(f=fb, bnd=bb, **opts)
+        assert st.status == 0
+        Ls = 0.5 * ((uu - target) ** 2).sum(dim=(1, 2, 3))
+        fd = (Ls[0::2] - Ls[1::2]) / (2 * eps)
+        ad = (f.grad * v_f).sum(dim=(1, 2, 3)) + (gb.grad * v_g).sum(dim=1)
+        errs.append(((ad - fd).abs() / fd.abs()).cpu().numpy())
+    errs = np.concatenate(errs)
+    assert errs.size == 64
+    assert errs.max() <= 1e-6, errs.max()
 
 
 def test_laplace256_overlap5_and_adaptive_converge():
