@@ -70,6 +70,20 @@ typedef enum { MS_MODE_SYNC = 0, MS_MODE_ASYNC = 1 } ms_mode;
  * stay double (two-stage iterative refinement). */
 typedef enum { MS_PREC_FP64 = 0, MS_PREC_MIXED = 1 } ms_precision;
 
+/* One record of the solve trace (opts.trace): one block solve of one sweep.
+ * The paper's observable is the residual against time (sections 3.2 and 4);
+ * the trace gives it per block, which is what separates the synchronous and
+ * asynchronous modes (in the latter every block runs its own sweep count). */
+typedef struct {
+  int sweep;               /* sync: outer sweep k (the block solve that forms x^{k+1});
+                              async: the block's own sweep count before this visit */
+  int block;               /* block id bx + px*(by + py*bz) */
+  int rhs;                 /* right-hand side */
+  int inner_its;           /* inner iterations of this block solve */
+  double block_rr;         /* ||r_i||^2 of the block residual this solve started from (FP64) */
+  unsigned long long t_ns; /* device clock (%globaltimer, ns) when the block solve ended */
+} ms_trace_rec;
+
 typedef struct {
   int mode;              /* ms_mode, default MS_MODE_SYNC */
   int precision;         /* ms_precision, default MS_PREC_MIXED */
@@ -127,6 +141,10 @@ typedef struct {
                             decision; when they run out the solve ends with MS_ERR_TIMEOUT and x holds
                             the last complete iterate.  0 (default) = 2^24 polls (backing off to
                             ~1 us each) */
+  int trace_cap;         /* records the trace ring holds (0 = no trace) */
+  ms_trace_rec* trace;   /* HOST, optional [trace_cap]: per block solve records, written by the kernels
+                            into a device ring and copied here after the solve in the order they were
+                            taken (when more than trace_cap were taken, the last trace_cap) */
 } ms_opts;
 
 typedef struct {
@@ -147,6 +165,7 @@ typedef struct {
                                   -2 vectorised (float4) streaming */
   double inner_rtol_final;     /* the inner tolerance of the last sweep (opts.inner_adapt: max over
                                   rhs of the controller's choice; else opts.inner_rtol) */
+  long long trace_count;       /* with opts.trace: records taken (min(trace_count, trace_cap) returned) */
 } ms_stats;
 
 /* Number of doubles in one rhs's packed boundary array. */

@@ -72,10 +72,17 @@ class SolveStats:
     inner_rtol_final: float = 0.0
     history_ms: np.ndarray | None = None
     history: np.ndarray | None = None
+    trace: np.ndarray | None = None
+    trace_count: int = 0
 
     @property
     def status_name(self):
         return _lib.STATUS_NAMES.get(self.status, str(self.status))
+
+
+# numpy view of ms_trace_rec (include/ms.h): one record per block solve
+TRACE_DTYPE = np.dtype([("sweep", "<i4"), ("block", "<i4"), ("rhs", "<i4"), ("inner_its", "<i4"),
+                        ("block_rr", "<f8"), ("t_ns", "<u8")])
 
 
 def _ptr(t):
@@ -207,7 +214,9 @@ class Grid:
         choose the inner tolerance at run time), overlap (sync: blocks extended
         by this many points per face, streaming engine), inner ('cg'|'gmres'),
         gmres_restart (GMRES basis size per cycle, 1..50), wait_polls
-        (persistent sync launch: poll budget of its bounded waits, 0 = default).
+        (persistent sync launch: poll budget of its bounded waits, 0 = default),
+        trace (N > 0: keep the last N block-solve records, returned as
+        stats.trace, a numpy array of TRACE_DTYPE, with stats.trace_count).
         """
         return self._call(self._lib.ms_solve, f, bnd, x0, out, history, opts)
 
@@ -219,6 +228,7 @@ class Grid:
         return self._call(self._lib.ms_gcg_solve, f, bnd, x0, out, False, opts)
 
     def _call(self, fn, f, bnd, x0, out, history, opts):
+        trace_n = int(opts.pop("trace", 0) or 0)
         f = self._field(f, "f", self.shape)
         bnd = self._field(bnd, "bnd", (self.nrhs, self.nbnd))
         if out is None:
@@ -237,6 +247,11 @@ class Grid:
             o.res_hist = hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
             thist = np.zeros(o.outer_maxit + 1)
             o.time_hist = thist.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        trace = None
+        if trace_n > 0:
+            trace = np.zeros(trace_n, dtype=TRACE_DTYPE)
+            o.trace_cap = trace_n
+            o.trace = trace.ctypes.data_as(ctypes.POINTER(_lib.TraceRec))
         st = _lib.Stats()
         per_its = (ctypes.c_int * self.nrhs)()
         per_rel = (ctypes.c_double * self.nrhs)()
@@ -253,6 +268,9 @@ class Grid:
         if hist is not None:
             stats.history = hist
             stats.history_ms = thist
+        if trace is not None:
+            stats.trace_count = int(st.trace_count)
+            stats.trace = trace[:min(trace_n, stats.trace_count)]
         return out, stats
 
     def solve_host(self, f=None, bnd=None, x=None, **opts):

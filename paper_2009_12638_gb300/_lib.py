@@ -30,6 +30,17 @@ EXPORTS = ("ms_boundary_size", "ms_default_opts", "ms_create_grid", "ms_partitio
 NOALLOC_MAX_RHS = 1024
 
 
+class TraceRec(ctypes.Structure):
+    _fields_ = [
+        ("sweep", ctypes.c_int),
+        ("block", ctypes.c_int),
+        ("rhs", ctypes.c_int),
+        ("inner_its", ctypes.c_int),
+        ("block_rr", ctypes.c_double),
+        ("t_ns", ctypes.c_ulonglong),
+    ]
+
+
 class Opts(ctypes.Structure):
     _fields_ = [
         ("mode", ctypes.c_int),
@@ -57,6 +68,8 @@ class Opts(ctypes.Structure):
         ("gmres_restart", ctypes.c_int),
         ("time_hist", ctypes.POINTER(ctypes.c_double)),
         ("wait_polls", ctypes.c_int),
+        ("trace_cap", ctypes.c_int),
+        ("trace", ctypes.POINTER(TraceRec)),
     ]
 
 
@@ -79,6 +92,7 @@ class Stats(ctypes.Structure):
         ("engine", ctypes.c_int),
         ("variant", ctypes.c_int),
         ("inner_rtol_final", ctypes.c_double),
+        ("trace_count", ctypes.c_longlong),
     ]
 
 

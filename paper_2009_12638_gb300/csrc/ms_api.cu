@@ -88,6 +88,8 @@ struct ms_grid {
   DevBuf flow_ws;  // tickets, per-task progress, per-sweep counters (persistent sync mode)
   DevBuf gcg_ws;   // global CG: r, p, q, partial sums, control words
   DevBuf thist;    // [outer_maxit+1] stop-test times (opts.time_hist)
+  DevBuf trace_ws; // trace ring (opts.trace): head counter, then trace_cap records
+  TraceArgs trace{nullptr, nullptr, 0};  // the current solve's trace ring (rec == nullptr: none)
   Tuner tuner;
   long long npts() const { return (long long)nx * ny * nz; }
   long long nbnd() const { return ms_boundary_size(nx, ny, nz); }
@@ -161,6 +163,8 @@ extern "C" void ms_default_opts(ms_opts* o) {
   o->gmres_restart = 10;
   o->time_hist = nullptr;
   o->wait_polls = 0;
+  o->trace_cap = 0;
+  o->trace = nullptr;
 }
 
 static std::vector<int> equal_cuts(int n, int p) {
@@ -280,6 +284,7 @@ static int check_opts(ms_grid* g, const ms_opts& o) {
   if (o.inner_adapt != 0 && o.inner_adapt != 1) return fail(g, MS_ERR_ARG, "opts.inner_adapt must be 0 or 1");
   if (o.overlap < 0) return fail(g, MS_ERR_ARG, "opts.overlap must be >= 0");
   if (o.wait_polls < 0) return fail(g, MS_ERR_ARG, "opts.wait_polls must be >= 0 (0 = default)");
+  if (o.trace_cap < 0) return fail(g, MS_ERR_ARG, "opts.trace_cap must be >= 0");
   if (o.inner_method != 0 && o.inner_method != 1) return fail(g, MS_ERR_ARG, "opts.inner_method must be 0 (CG) or 1 (GMRES)");
   if (o.inner_method == 1 && (o.gmres_restart < 1 || o.gmres_restart > kGmresMaxRestart))
     return fail(g, MS_ERR_ARG, "opts.gmres_restart must be 1..%d", kGmresMaxRestart);
@@ -531,6 +536,7 @@ extern "C" int ms_sweep(ms_grid* g, const double* f, const double* bnd, const do
   sa.inner_rtol_rhs = nullptr;
   sa.inner_method = o.inner_method;
   sa.gmres_restart = o.gmres_restart;
+  sa.tr = TraceArgs{nullptr, nullptr, 0};
   if (shape.variant >= 0) MS_CUDA(g, launch_res_sweep(shape.variant, shape.cluster, shape.slots, shape.smem, sa, stream));
   else if (shape.variant == -2) MS_CUDA(g, launch_strip_sweep(shape.threads, shape.cluster, shape.slots, sa, stream));
   else MS_CUDA(g, launch_sweep(prec, shape.threads, shape.cluster, shape.slots, sa, stream));
@@ -767,6 +773,7 @@ extern "C" int ms_destroy(ms_grid* g) {
   g->flow_ws.release();
   g->gcg_ws.release();
   g->thist.release();
+  g->trace_ws.release();
   g->tuner.release();
   delete g;
   return MS_OK;
@@ -885,6 +892,14 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
     MS_CUDA(g, cudaMemcpyAsync(rtol_rhs, h_rtol.data(), h_rtol.size() * sizeof(double), cudaMemcpyHostToDevice,
                                stream));
   }
+  // solve trace: a ring of records in device memory, copied to opts.trace at the end
+  g->trace = TraceArgs{nullptr, nullptr, 0};
+  if (o.trace && o.trace_cap > 0) {
+    MS_CUDA(g, g->trace_ws.reserve(256 + (size_t)o.trace_cap * sizeof(ms_trace_rec)));
+    MS_CUDA(g, cudaMemsetAsync(g->trace_ws.p, 0, sizeof(unsigned long long), stream));
+    g->trace = TraceArgs{reinterpret_cast<ms_trace_rec*>(g->trace_ws.as<char>() + 256),
+                         g->trace_ws.as<unsigned long long>(), o.trace_cap};
+  }
   // ||bhat|| per rhs (and the residual of x^0, unused here)
   rc = run_resid(g, f, bnd, x, norms, invb, stream);
   if (rc != MS_OK) return rc;
@@ -937,6 +952,7 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
     sa.inner_rtol_rhs = adapt ? rtol_rhs : nullptr;
     sa.inner_method = o.inner_method;
     sa.gmres_restart = o.gmres_restart;
+    sa.tr = g->trace;
     CheckArgs ca;
     ca.nrhs = g->nrhs;
     ca.ntasks = ntasks;
@@ -1286,7 +1302,23 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
                              stream));
   MS_CUDA(g, cudaStreamSynchronize(stream));
   MS_CUDA(g, cudaGetLastError());
+  long long trace_count = 0;
+  if (g->trace.rec) {
+    // the ring in ticket order: the oldest record sits at count % cap once it wrapped
+    unsigned long long head = 0;
+    MS_CUDA(g, cudaMemcpy(&head, g->trace.head, sizeof head, cudaMemcpyDeviceToHost));
+    const unsigned long long cap = (unsigned long long)o.trace_cap;
+    const unsigned long long n = std::min(head, cap), first = head > cap ? head % cap : 0;
+    const size_t rs = sizeof(ms_trace_rec);
+    if (n > 0) {
+      MS_CUDA(g, cudaMemcpy(o.trace, g->trace.rec + first, (size_t)(n - first) * rs, cudaMemcpyDeviceToHost));
+      if (first > 0) MS_CUDA(g, cudaMemcpy(o.trace + (n - first), g->trace.rec, (size_t)first * rs, cudaMemcpyDeviceToHost));
+    }
+    trace_count = (long long)head;
+    g->trace = TraceArgs{nullptr, nullptr, 0};
+  }
   if (st) {
+    st->trace_count = trace_count;
     float ms_el = 0.f;
     cudaEventElapsedTime(&ms_el, ev0, ev1);
     double relmax = 0.0;
@@ -1414,6 +1446,7 @@ int solve_async(ms_grid* g, const double* f, const double* bnd, double* x, const
   a.time_budget_ns = o.time_limit_ms > 0.0 ? (unsigned long long)(o.time_limit_ms * 1.0e6) : 0ull;
   a.slice_ns = 2000000000ull;  // no single launch runs longer than ~2 s
   a.err = &ctl->err;
+  a.tr = g->trace;
   MS_CUDA(g, launch_async_init(a, stream));
 
   CtlLayout L2 = L;

@@ -262,9 +262,10 @@ __device__ __forceinline__ void async_face_store(const AsyncArgs& a, const Task&
 
 // Face publication, part 2 (after every thread stored its face values):
 // complete the slots (even seq, release), bump the versions and the task's
-// sweep count, record the inner iterations.
+// sweep count, record the inner iterations (and the trace record, with the
+// block residual block_rr this visit started from).
 __device__ __forceinline__ void async_publish_end(const AsyncArgs& a, const Task& tk, int t, const int* fslot,
-                                                  unsigned rank, int m) {
+                                                  unsigned rank, int m, double block_rr) {
   __threadfence();
   cl_barrier();
   if (rank == 0 && threadIdx.x == 0) {
@@ -274,6 +275,7 @@ __device__ __forceinline__ void async_publish_end(const AsyncArgs& a, const Task
       st_rel_u32(sp, *sp + 1u);  // even: slot complete
       st_rel_u32(a.face_ver + t * 6 + f, a.face_ver[t * 6 + f] + 1u);
     }
+    trace_push(a.tr, a.sweeps[t], tk.block, tk.rhs, m, block_rr);
     a.sweeps[t] += 1;
     if (m > 0) {
       atomicAdd(a.inner_count + 2 * tk.rhs, (unsigned long long)m);

@@ -50,6 +50,22 @@ __device__ __forceinline__ void cl_store(int* local, unsigned rank, int v) {
   asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(cl_map(local, rank)), "r"(v) : "memory");
 }
 
+// One record of the solve trace (called by one thread per block solve).
+__device__ __forceinline__ void trace_push(const TraceArgs& tr, int sweep, int block, int rhs, int inner_its,
+                                           double block_rr) {
+  if (!tr.rec) return;
+  const unsigned long long i = atomicAdd(tr.head, 1ull);
+  unsigned long long now;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+  ms_trace_rec& r = tr.rec[i % (unsigned long long)tr.cap];
+  r.sweep = sweep;
+  r.block = block;
+  r.rhs = rhs;
+  r.inner_its = inner_its;
+  r.block_rr = block_rr;
+  r.t_ns = now;
+}
+
 __device__ __forceinline__ double warp_sum_to_lane0(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);

@@ -5,6 +5,8 @@
 
 #include <cstdint>
 
+#include "ms.h"
+
 struct ms_grid;
 
 namespace ms {
@@ -38,6 +40,15 @@ constexpr int kActive = 0;
 constexpr int kConverged = 1;
 constexpr int kStopped = 2;
 
+// Solve trace (opts.trace): a ring of ms_trace_rec in device memory.  Every
+// block solve takes the next ticket from `head` and writes record
+// ticket % cap; rec == nullptr = no trace.
+struct TraceArgs {
+  ms_trace_rec* rec;
+  unsigned long long* head;
+  int cap;
+};
+
 // device error word bits
 constexpr int kErrGeometry = 1;
 constexpr int kErrTimeout = 2;
@@ -68,6 +79,7 @@ struct SweepArgs {
   const double* inner_rtol_rhs;  // [nrhs] per-rhs inner tolerance (opts.inner_adapt) or null: inner_rtol
   int inner_method;              // 0 CG, 1 restarted GMRES (scalar streaming engine)
   int gmres_restart;             // GMRES basis size per cycle (slot holds gmres_restart + 3 vectors)
+  TraceArgs tr;                  // solve trace (rec == nullptr: none)
 };
 
 __host__ __device__ inline double sweep_inner_rtol(const SweepArgs& a, int rhs) {
@@ -180,6 +192,7 @@ struct AsyncArgs {
   unsigned long long time_budget_ns;  // 0 = none; when spent the launch stops with kErrTimeout
   unsigned long long slice_ns;        // the launch returns (no error) after this long; the host relaunches
   int* err;
+  TraceArgs tr;                       // solve trace (rec == nullptr: none)
 };
 
 struct ResidArgs {

@@ -47,25 +47,35 @@ def test_ctypes_structs_match_c_layout(tmp_path):
 #include <stddef.h>
 #include "ms.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(ms_opts), offsetof(ms_opts, outer_tol), offsetof(ms_opts, res_hist),
-         offsetof(ms_opts, slow_ns), offsetof(ms_opts, time_limit_ms), offsetof(ms_opts, variant),
-         offsetof(ms_opts, inner_adapt), offsetof(ms_opts, overlap), offsetof(ms_opts, gmres_restart),
-         offsetof(ms_opts, wait_polls));
-  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(ms_stats), offsetof(ms_stats, lups), offsetof(ms_stats, per_rhs_rel),
-         offsetof(ms_stats, slots), offsetof(ms_stats, variant), offsetof(ms_stats, inner_rtol_final));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(ms_opts), offsetof(ms_opts, outer_tol),
+         offsetof(ms_opts, res_hist), offsetof(ms_opts, slow_ns), offsetof(ms_opts, time_limit_ms),
+         offsetof(ms_opts, variant), offsetof(ms_opts, inner_adapt), offsetof(ms_opts, overlap),
+         offsetof(ms_opts, gmres_restart), offsetof(ms_opts, wait_polls), offsetof(ms_opts, trace_cap),
+         offsetof(ms_opts, trace));
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(ms_stats), offsetof(ms_stats, lups), offsetof(ms_stats, per_rhs_rel),
+         offsetof(ms_stats, slots), offsetof(ms_stats, variant), offsetof(ms_stats, inner_rtol_final),
+         offsetof(ms_stats, trace_count));
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(ms_trace_rec), offsetof(ms_trace_rec, sweep),
+         offsetof(ms_trace_rec, block), offsetof(ms_trace_rec, rhs), offsetof(ms_trace_rec, inner_its),
+         offsetof(ms_trace_rec, block_rr), offsetof(ms_trace_rec, t_ns));
   return 0;
 }
 ''')
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
-    a, b = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:2]
-    O, S = _lib.Opts, _lib.Stats
+    a, b, c = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:3]
+    O, S, T = _lib.Opts, _lib.Stats, _lib.TraceRec
     assert [int(v) for v in a.split()] == [ctypes.sizeof(O), O.outer_tol.offset, O.res_hist.offset,
                                           O.slow_ns.offset, O.time_limit_ms.offset, O.variant.offset,
                                           O.inner_adapt.offset, O.overlap.offset, O.gmres_restart.offset,
-                                          O.wait_polls.offset]
+                                          O.wait_polls.offset, O.trace_cap.offset, O.trace.offset]
     assert [int(v) for v in b.split()] == [ctypes.sizeof(S), S.lups.offset, S.per_rhs_rel.offset, S.slots.offset,
-                                          S.variant.offset, S.inner_rtol_final.offset]
+                                          S.variant.offset, S.inner_rtol_final.offset, S.trace_count.offset]
+    from paper_2009_12638_gb300 import TRACE_DTYPE
+    want = [ctypes.sizeof(T)] + [getattr(T, n).offset for n in ("sweep", "block", "rhs", "inner_its", "block_rr", "t_ns")]
+    assert [int(v) for v in c.split()] == want
+    assert TRACE_DTYPE.itemsize == ctypes.sizeof(T)
+    assert [TRACE_DTYPE.fields[n][1] for n in ("sweep", "block", "rhs", "inner_its", "block_rr", "t_ns")] == want[1:]
 
 
 def test_default_opts(lib):
@@ -75,7 +85,7 @@ def test_default_opts(lib):
     assert o.slow_block == -1 and o.use_graph == 1
     assert o.variant == -1 and o.inner_adapt == 0 and o.overlap == 0
     assert o.inner_method == 0 and o.gmres_restart == 10
-    assert o.wait_polls == 0
+    assert o.wait_polls == 0 and o.trace_cap == 0 and not o.trace
 
 
 def test_resident_variant_table(lib):
