@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(NT, 1) async_kernel(const AsyncArgs a) {
         async_face_store(a, tk, t, fslot, x, y, z, xn);
       }
     }
-    async_publish_end(a, tk, t, fslot, rank, m, sm.tot[0]);
+    async_publish_end(a, tk, t, fslot, rank, m);
     // ---------------- 5. stale global estimate
     async_monitor(a, rank);
   }

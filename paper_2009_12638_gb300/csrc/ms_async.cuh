@@ -263,9 +263,9 @@ __device__ __forceinline__ void async_face_store(const AsyncArgs& a, const Task&
 // Face publication, part 2 (after every thread stored its face values):
 // complete the slots (even seq, release), bump the versions and the task's
 // sweep count, record the inner iterations (and the trace record, with the
-// block residual block_rr this visit started from).
+// block residual this visit started from, read back from the partials).
 __device__ __forceinline__ void async_publish_end(const AsyncArgs& a, const Task& tk, int t, const int* fslot,
-                                                  unsigned rank, int m, double block_rr) {
+                                                  unsigned rank, int m) {
   __threadfence();
   cl_barrier();
   if (rank == 0 && threadIdx.x == 0) {
@@ -275,7 +275,7 @@ __device__ __forceinline__ void async_publish_end(const AsyncArgs& a, const Task
       st_rel_u32(sp, *sp + 1u);  // even: slot complete
       st_rel_u32(a.face_ver + t * 6 + f, a.face_ver[t * 6 + f] + 1u);
     }
-    trace_push(a.tr, a.sweeps[t], tk.block, tk.rhs, m, block_rr);
+    if (a.tr.rec) trace_push(a.tr, a.sweeps[t], tk.block, tk.rhs, m, a.partial[t]);
     a.sweeps[t] += 1;
     if (m > 0) {
       atomicAdd(a.inner_count + 2 * tk.rhs, (unsigned long long)m);

@@ -50,10 +50,12 @@ __device__ __forceinline__ void cl_store(int* local, unsigned rank, int v) {
   asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(cl_map(local, rank)), "r"(v) : "memory");
 }
 
-// One record of the solve trace (called by one thread per block solve).
+// One record of the solve trace (called by one thread per block solve, only
+// when tr.rec is set).  Callers read sweep and block_rr back from memory
+// inside their `if (tr.rec)` so that no register holds them through the
+// inner solve.
 __device__ __forceinline__ void trace_push(const TraceArgs& tr, int sweep, int block, int rhs, int inner_its,
                                            double block_rr) {
-  if (!tr.rec) return;
   const unsigned long long i = atomicAdd(tr.head, 1ull);
   unsigned long long now;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));

@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(NT, 1) sweep_kernel(const SweepArgs a) {
       atomicAdd(a.inner_count + 2 * tk.rhs, (unsigned long long)m);
       atomicAdd(a.inner_count + 2 * tk.rhs + 1, (unsigned long long)m * (unsigned long long)(sl.plane * tk.bz));
     }
-    if (rank == 0 && tid == 0) trace_push(a.tr, k, tk.block, tk.rhs, m, red0[0]);
+    if (rank == 0 && tid == 0 && a.tr.rec) trace_push(a.tr, *a.k_dev, tk.block, tk.rhs, m, a.partial[t]);
   }
 }
 

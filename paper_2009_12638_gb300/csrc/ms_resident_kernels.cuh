@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(NT, 1) res_sweep_kernel(const SweepArgs a, int
       atomicAdd(a.inner_count + 2 * tk.rhs, (unsigned long long)m);
       atomicAdd(a.inner_count + 2 * tk.rhs + 1, (unsigned long long)m * (unsigned long long)tk.bx * tk.by * tk.bz);
     }
-    if (rank == 0 && tid == 0) trace_push(a.tr, k, tk.block, tk.rhs, m, red0[0]);
+    if (rank == 0 && tid == 0 && a.tr.rec) trace_push(a.tr, *a.k_dev, tk.block, tk.rhs, m, a.partial[t]);
   }
 }
 
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(NT, 1) res_async_kernel(const AsyncArgs a, int
         }
       }
     }
-    async_publish_end(a, tk, t, fslot, rank, m, red.tot[0]);
+    async_publish_end(a, tk, t, fslot, rank, m);
     if constexpr (DS) {
       __syncthreads();
       zero_smem<NT>(dyn4, smem_f4);
@@ -545,7 +545,7 @@ __global__ void __launch_bounds__(NT, 1) res_flow_kernel(const FlowArgs fa, int 
         atomicAdd(a.inner_count + 2 * tk.rhs, (unsigned long long)m);
         atomicAdd(a.inner_count + 2 * tk.rhs + 1, (unsigned long long)m * (unsigned long long)tk.bx * tk.by * tk.bz);
       }
-      trace_push(a.tr, k, tk.block, tk.rhs, m, red.tot[0]);
+      if (a.tr.rec) trace_push(a.tr, fa.k0 + kr, tk.block, tk.rhs, m, a.partial[t]);
     }
   }
 }
