@@ -26,9 +26,11 @@ multisplitting"):
 Pins (tests/test_oracle.py): Kronecker-sum operator, sine eigenpairs,
 symmetry, discretely harmonic closed forms, the point-Jacobi formula for 1^3
 blocks, dense LU for one block and for converged solves, exact block Jacobi
-against dense block solves.  ``solve_delayed`` is pinned only by convergence
-to the LU solution (its iterates have no closed form: parity unpinned for the
-asynchronous iterate sequence).
+against dense block solves, the truncated inner CG against the Krylov-space
+A-norm minimiser with its exact stop index, and ``solve_delayed`` (with exact
+inner solves) against dense block solves whose face layers come from the
+delayed iterates, sweep by sweep, plus zero delays = synchronous and
+convergence to the LU solution.
 """
 from __future__ import annotations
 

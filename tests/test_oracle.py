@@ -427,6 +427,57 @@ def test_delayed_with_zero_delays_is_synchronous(oracle_mod):
     np.testing.assert_array_equal(a["x"], b["x"])
 
 
+@pytest.mark.parametrize("cuts,max_delay", [(((0, 3, 6), (0, 2, 5), (0, 4, 6)), 2),
+                                             (((0, 2, 5, 7), (0, 4), (0, 3, 5)), 3)])
+def test_delayed_sweeps_match_dense_block_solves_with_stale_faces(oracle_mod, cuts, max_delay):
+    """The asynchronous model (sections 2.1, 2.3 and 3: a block uses the latest
+    values it has received, possibly several sweeps old), with exact inner
+    solves, restated densely in numpy: block i's sweep k solves its dense
+    diagonal block A_ii against bhat - A x~, where x~ is x^k except on the layer
+    of points across each face, which comes from x^(k - d) for that face's delay
+    d (capped by max_delay and by sweep 0).  Sweep for sweep the oracle must
+    give the same iterates."""
+    cx, cy, cz = (np.asarray(c) for c in cuts)
+    nx, ny, nz = int(cx[-1]), int(cy[-1]), int(cz[-1])
+    px, py, pz = len(cx) - 1, len(cy) - 1, len(cz) - 1
+    nblocks = px * py * pz
+    g = rng(19).standard_normal(inputs.boundary_size(nx, ny, nz))
+    f = rng(20).standard_normal((nz, ny, nx))
+    K = 5
+    delays = rng(21).integers(0, max_delay + 2, size=(K + 1, nblocks, 6)).astype(np.int32)  # some above the cap
+    A = kron_laplacian(nx, ny, nz).toarray()
+    b = bhat_independent(nx, ny, nz, f, g)
+    X = [np.zeros((nz, ny, nx))]
+    for k in range(K):
+        xn = X[k].copy()
+        for blk in range(nblocks):
+            bi, bj, bk = blk % px, (blk // px) % py, blk // (px * py)
+            lo = (cx[bi], cy[bj], cz[bk])
+            hi = (cx[bi + 1], cy[bj + 1], cz[bk + 1])
+            xv = X[k].copy()
+            for face in range(6):
+                axis = face // 2
+                d = min(int(delays[k, blk, face]), max_delay)
+                ks = max(k - d, 0)
+                layer = lo[axis] - 1 if face % 2 == 0 else hi[axis]
+                if layer < 0 or layer >= (nx, ny, nz)[axis]:
+                    continue
+                sl = [slice(lo[2], hi[2]), slice(lo[1], hi[1]), slice(lo[0], hi[0])]  # (z, y, x)
+                sl[2 - axis] = slice(layer, layer + 1)
+                xv[tuple(sl)] = X[ks][tuple(sl)]
+            r = (b - (A @ xv.ravel()).reshape(nz, ny, nx))
+            own = (slice(lo[2], hi[2]), slice(lo[1], hi[1]), slice(lo[0], hi[0]))
+            mask = np.zeros((nz, ny, nx), dtype=bool)
+            mask[own] = True
+            m = mask.ravel()
+            delta = np.linalg.solve(A[np.ix_(m, m)], r.ravel()[m])
+            xn[own] += delta.reshape(hi[2] - lo[2], hi[1] - lo[1], hi[0] - lo[0])
+        X.append(xn)
+        res = oracle_mod.solve_delayed(nx, ny, nz, cx, cy, cz, np.resize(delays, (k + 2, nblocks, 6)), max_delay, f=f,
+                                       bnd=g, inner_rtol=1e-15, inner_maxit=2000, outer_tol=0.0, outer_maxit=k + 1)
+        np.testing.assert_allclose(res["x"], xn, rtol=0, atol=1e-10 * np.abs(xn).max())
+
+
 def test_delayed_converges_to_lu(oracle_mod):
     """Bounded staleness still converges for this M-matrix (section 2.1 cites the
     asynchronous convergence theory); at least as many sweeps as synchronous."""
