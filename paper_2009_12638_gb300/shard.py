@@ -294,6 +294,12 @@ def sharded_solve(layout: ShardLayout, shards, comm, bnd=None, f=None, x0=None, 
             break
     if nrhs is None:
         raise ValueError("give at least one of bnd, f, x0")
+    if int(sweep_opts.get("overlap", 0) or 0) > 0 and layout.size > 1:
+        # a block box extended by o points reaches o layers into the next rank;
+        # the plane swap carries one layer
+        raise ValueError("overlapping blocks are not supported across ranks (the plane swap carries one layer)")
+    if sweep_opts.get("mode", "sync") not in ("sync", 0):
+        raise ValueError("the sharded solve runs synchronous sweeps")
 
     def on(dev, t):
         return None if t is None else t.to(dev, dtype=torch.float64).contiguous()

@@ -172,6 +172,17 @@ def test_local_shards_converge_like_the_whole_grid(oracle_mod):
         assert st.per_rhs_rel[s] == pytest.approx(ref["rel_residual"], rel=1e-9)
 
 
+def test_overlap_and_async_are_rejected_across_ranks(oracle_mod):
+    c = CASE
+    lay = ShardLayout(c["nx"], c["ny"], c["nz"], c["cx"], c["cy"], c["cz"], (2, 1, 1))
+    shards = [OracleShard(lay, r, 1) for r in range(lay.size)]
+    bnd, _ = problem(1)
+    with pytest.raises(ValueError):
+        sharded_solve(lay, shards, LocalComm(lay), bnd=bnd, overlap=2)
+    with pytest.raises(ValueError):
+        sharded_solve(lay, shards, LocalComm(lay), bnd=bnd, mode="async")
+
+
 def test_zero_data_stops_at_k0(oracle_mod):
     c = CASE
     lay = ShardLayout(c["nx"], c["ny"], c["nz"], c["cx"], c["cy"], c["cz"], (2, 1, 1))
