@@ -83,6 +83,8 @@ def parse():
                     help="skip the batched workloads (uneven blocks x 16 rhs, 512^3 x 4 rhs)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--clock-log", default=None, help="directory for the raw nvidia-smi clock samples (CSV)")
+    ap.add_argument("--scale", type=int, default=1,
+                    help="profiling aid with --sweeps: shrink every block edge by this factor (block counts kept)")
     ap.add_argument("--sweeps", type=int, default=0,
                     help="profiling aid: run exactly this many outer sweeps once (no warm-up, no timing) and exit")
     return ap.parse_args()
@@ -313,7 +315,9 @@ def main():
     dev = torch.device("cuda", local)
 
     from paper_2009_12638_gb300 import Grid, inputs
-    cfg = inputs.make_config(args.workload)
+    if args.scale != 1 and not args.sweeps:
+        raise SystemExit("--scale is a profiling aid for --sweeps runs; the measured workload is the stated one")
+    cfg = inputs.make_config(args.workload, scale=args.scale)
     # each rank solves its own replica (different boundary seed for rank > 0)
     bnd_np = cfg["bnd"] if rank == 0 else inputs.boundary_uniform(cfg["nx"], cfg["ny"], cfg["nz"], cfg["nrhs"],
                                                                    2009 + rank)

@@ -241,8 +241,10 @@ MS_API int ms_norms(ms_grid* grid, const double* f, const double* bnd, const dou
  *   f, bnd: as ms_solve (device; may be NULL);
  *   x_in:   [nrhs][nz][ny][nx] x^k (device, read only);
  *   x_out:  [nrhs][nz][ny][nx] receives x^{k+1} (device; must not overlap x_in);
- *   rr_out: DEVICE [nrhs] or NULL: sum of (bhat - A x^k)^2 over this grid, as
- *           ms_norms (the residual the stop rule of section 2.1 tests on x^k);
+ *   rr_out: DEVICE [nrhs] or NULL: sum of (bhat - A x^k)^2 over this grid (the
+ *           residual the stop rule of section 2.1 tests on x^k), formed from
+ *           the sweep's own block partials in a fixed order (ms_norms gives the
+ *           same sum up to rounding);
  *   opts:   HOST or NULL; precision, inner_rtol, inner_maxit, overlap,
  *           inner_method, gmres_restart and the launch-shape fields are used;
  *           mode must be MS_MODE_SYNC and inner_adapt 0;
@@ -253,7 +255,9 @@ MS_API int ms_norms(ms_grid* grid, const double* f, const double* bnd, const dou
  * The launch shape is the one a solve of the same problem measured (ms_solve
  * caches it per handle), else the model's first choice.  The inner solves use
  * the same kernels and FP32 scaling as ms_solve, so a sweep here equals a
- * sweep of ms_solve on the same data. */
+ * sweep of ms_solve on the same data.  Besides the sweep kernel, the call
+ * reads f (when given) or only the points next to the boundary, for ||bhat||
+ * and the FP32 scaling. */
 MS_API int ms_sweep(ms_grid* grid, const double* f, const double* bnd, const double* x_in, double* x_out,
                     double* rr_out, const ms_opts* opts, ms_stats* stats, void* stream);
 

@@ -431,11 +431,12 @@ extern "C" int ms_norms(ms_grid* g, const double* f, const double* bnd, const do
   return MS_OK;
 }
 
-// One synchronous outer sweep outside ms_solve's loop: the residual of x_in
-// (norms and the FP32 scaling), then one launch of the sweep kernel that
-// ms_solve would use for this problem (its tuned shape when a solve of the
-// same problem measured one, else the model's first choice), reading x^k from
-// x_in and writing x^{k+1} to x_out.
+// One synchronous outer sweep outside ms_solve's loop: ||bhat|| (the FP32
+// scaling; only the points next to the boundary are visited when f is null),
+// one launch of the sweep kernel that ms_solve would use for this problem (its
+// tuned shape when a solve of the same problem measured one, else the model's
+// first choice) reading x^k from x_in and writing x^{k+1} to x_out, and the
+// squared residual of x^k summed from the kernel's block partials.
 extern "C" int ms_sweep(ms_grid* g, const double* f, const double* bnd, const double* x_in, double* x_out,
                         double* rr_out, const ms_opts* opts, ms_stats* st, void* stream_ptr) {
   if (!g) return MS_ERR_ARG;
@@ -510,8 +511,13 @@ extern "C" int ms_sweep(ms_grid* g, const double* f, const double* bnd, const do
   }
   MS_CUDA(g, cudaMemcpyAsync(g->tasks.p, tasks.data(), tasks.size() * sizeof(Task), cudaMemcpyHostToDevice, stream));
   MS_CUDA(g, cudaMemsetAsync(ctlb, 0, L.bytes, stream));  // every rhs active, sweep counter k = 0
-  rc = run_resid(g, f, bnd, x_in, norms, invb, stream);
-  if (rc != MS_OK) return rc;
+  // scratch: per-CTA parts of ||bhat||^2, then ||bhat||^2 and the residual shares per rhs
+  const int nblk = resid_blocks(g->npts());
+  MS_CUDA(g, g->rpart.reserve(((size_t)g->nrhs * nblk + 2 * (size_t)g->nrhs) * sizeof(double)));
+  double* bpart = g->rpart.as<double>();
+  double* bb_dev = bpart + (size_t)g->nrhs * nblk;
+  double* rr_dev = bb_dev + g->nrhs;
+  MS_CUDA(g, launch_bhat_sq(g->geo(), f, bnd, bpart, nblk, bb_dev, invb, stream));
   SweepArgs sa;
   sa.g = g->geo();
   sa.f = f;
@@ -540,15 +546,19 @@ extern "C" int ms_sweep(ms_grid* g, const double* f, const double* bnd, const do
   if (shape.variant >= 0) MS_CUDA(g, launch_res_sweep(shape.variant, shape.cluster, shape.slots, shape.smem, sa, stream));
   else if (shape.variant == -2) MS_CUDA(g, launch_strip_sweep(shape.threads, shape.cluster, shape.slots, sa, stream));
   else MS_CUDA(g, launch_sweep(prec, shape.threads, shape.cluster, shape.slots, sa, stream));
+  // the residual share of x^k: the sweep's block partials (owned points), in fixed order
+  MS_CUDA(g, launch_task_sums(sa.tasks, sa.partial, ntasks, g->nrhs, rr_dev, stream));
   if (rr_out)
-    MS_CUDA(g, cudaMemcpy2DAsync(rr_out, sizeof(double), norms, 2 * sizeof(double), sizeof(double), g->nrhs,
-                                 cudaMemcpyDeviceToDevice, stream));
+    MS_CUDA(g, cudaMemcpyAsync(rr_out, rr_dev, g->nrhs * sizeof(double), cudaMemcpyDeviceToDevice, stream));
   if (!st) return MS_OK;
   MS_CUDA(g, cudaEventRecord(ev1, stream));
   std::vector<double> hn(2 * (size_t)g->nrhs);
   std::vector<unsigned long long> hin(2 * (size_t)g->nrhs);
   int herr = 0;
-  MS_CUDA(g, cudaMemcpyAsync(hn.data(), norms, hn.size() * sizeof(double), cudaMemcpyDeviceToHost, stream));
+  for (int r = 0; r < g->nrhs; ++r) {
+    MS_CUDA(g, cudaMemcpyAsync(&hn[2 * r], rr_dev + r, sizeof(double), cudaMemcpyDeviceToHost, stream));
+    MS_CUDA(g, cudaMemcpyAsync(&hn[2 * r + 1], bb_dev + r, sizeof(double), cudaMemcpyDeviceToHost, stream));
+  }
   MS_CUDA(g, cudaMemcpyAsync(hin.data(), inner, hin.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                              stream));
   MS_CUDA(g, cudaMemcpyAsync(&herr, &ctl->err, sizeof(int), cudaMemcpyDeviceToHost, stream));

@@ -245,6 +245,13 @@ cudaError_t async_max_clusters(int prec, int threads, int cluster, int* out);
 cudaError_t launch_resid(const ResidArgs& a, double* out /*[nrhs][2]*/, double* inv_bnorm /*[nrhs] or null*/,
                          cudaStream_t s);
 cudaError_t launch_face_gather(const Geo& g, const double* lam, double* grad, cudaStream_t s);
+// ||bhat||^2 per rhs and 1/||bhat|| (visits only the points next to the boundary when f is null);
+// part: [nrhs][nblk] scratch
+cudaError_t launch_bhat_sq(const Geo& g, const double* f, const double* bnd, double* part, int nblk, double* out,
+                           double* inv_bnorm, cudaStream_t s);
+// out[s] = fixed-order sum of the block partials of rhs s
+cudaError_t launch_task_sums(const Task* tasks, const double* partial, int ntasks, int nrhs, double* out,
+                             cudaStream_t s);
 cudaError_t launch_async_init(const AsyncArgs& a, cudaStream_t s);
 cudaError_t launch_async_rearm(const AsyncArgs& a, cudaStream_t s);
 // on-chip (resident) FP32 inner CG, sync mode (ms_resident.cu)

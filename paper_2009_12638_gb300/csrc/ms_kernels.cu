@@ -270,6 +270,100 @@ __global__ void resid_finish_kernel(int nrhs, int nblk, const double* part, doub
   }
 }
 
+// ---------------------------------------------------------------- ||bhat||^2 alone
+// grid (nblk, nrhs): per-CTA sums of bhat^2 (bhat = f + lift(bnd)).  Without f
+// only the points next to the boundary carry data, so only they are visited:
+// the x faces (i = 0, nx-1), then the y faces without the x edges, then the z
+// faces without the x and y edges -- every point of that shell once.
+__global__ void __launch_bounds__(256) bhat_sq_kernel(const Geo g, const double* f, const double* bnd, double* part,
+                                                      int nblk) {
+  const int s = blockIdx.y;
+  const double* __restrict__ fs = f ? f + (long long)s * g.npts : nullptr;
+  const double* __restrict__ bs = bnd ? bnd + (long long)s * g.nbnd : nullptr;
+  const long long nxy = (long long)g.nx * g.ny;
+  const long long fyz = (long long)g.nz * g.ny, fxz = (long long)g.nz * g.nx;
+  // boundary values next to interior point (gx, gy, gz)
+  auto lifted = [&](int gx, int gy, int gz) {
+    double so = 0.0;
+    if (!bs) return so;
+    if (gx == 0) so += bs[(long long)gz * g.ny + gy];
+    if (gx == g.nx - 1) so += bs[fyz + (long long)gz * g.ny + gy];
+    if (gy == 0) so += bs[2 * fyz + (long long)gz * g.nx + gx];
+    if (gy == g.ny - 1) so += bs[2 * fyz + fxz + (long long)gz * g.nx + gx];
+    if (gz == 0) so += bs[2 * fyz + 2 * fxz + (long long)gy * g.nx + gx];
+    if (gz == g.nz - 1) so += bs[2 * fyz + 2 * fxz + nxy + (long long)gy * g.nx + gx];
+    return so;
+  };
+  double sb = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (fs) {
+    for (long long gi = t0; gi < g.npts; gi += stride) {
+      const int gx = (int)(gi % g.nx), gy = (int)((gi / g.nx) % g.ny), gz = (int)(gi / nxy);
+      const double bh = fs[gi] + lifted(gx, gy, gz);
+      sb += bh * bh;
+    }
+  } else if (bs) {
+    const int ix = g.nx > 1 ? 2 : 1, iy = g.ny > 1 ? 2 : 1, iz = g.nz > 1 ? 2 : 1;  // x faces present
+    const long long ny_in = g.ny > 2 ? g.ny - 2 : 0, nx_in = g.nx > 2 ? g.nx - 2 : 0;
+    const long long n_x = (long long)ix * g.ny * g.nz;               // the x faces
+    const long long n_y = (long long)iy * nx_in * g.nz;              // y faces, x edges excluded
+    const long long n_z = (long long)iz * nx_in * ny_in;             // z faces, x and y edges excluded
+    for (long long e = t0; e < n_x + n_y + n_z; e += stride) {
+      int gx, gy, gz;
+      if (e < n_x) {
+        const long long q = e % ((long long)g.ny * g.nz);
+        gx = e < (long long)g.ny * g.nz ? 0 : g.nx - 1;
+        gy = (int)(q % g.ny);
+        gz = (int)(q / g.ny);
+      } else if (e < n_x + n_y) {
+        const long long p = e - n_x, plane = nx_in * g.nz;
+        const long long q = p % plane;
+        gy = p < plane ? 0 : g.ny - 1;
+        gx = 1 + (int)(q % nx_in);
+        gz = (int)(q / nx_in);
+      } else {
+        const long long p = e - n_x - n_y, plane = nx_in * ny_in;
+        const long long q = p % plane;
+        gz = p < plane ? 0 : g.nz - 1;
+        gx = 1 + (int)(q % nx_in);
+        gy = 1 + (int)(q / nx_in);
+      }
+      const double bh = lifted(gx, gy, gz);
+      sb += bh * bh;
+    }
+  }
+  __shared__ double w[8];
+  sb = warp_sum_to_lane0(sb);
+  if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = sb;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int i = 0; i < 8; ++i) a += w[i];
+    part[(long long)s * nblk + blockIdx.x] = a;
+  }
+}
+
+// out[s] = sum of the per-CTA parts; inv_bnorm[s] = 1/||bhat|| (1 if bhat = 0)
+__global__ void bhat_sq_finish_kernel(int nrhs, int nblk, const double* part, double* out, double* inv_bnorm) {
+  for (int s = threadIdx.x; s < nrhs; s += blockDim.x) {
+    double a = 0.0;
+    for (int b = 0; b < nblk; ++b) a += part[(long long)s * nblk + b];
+    out[s] = a;
+    inv_bnorm[s] = a > 0.0 ? 1.0 / sqrt(a) : 1.0;
+  }
+}
+
+// out[s] = the sum of the block partials of rhs s (one warp per rhs, the fixed
+// order of rhs_partial_sum_warp)
+__global__ void task_sums_kernel(const Task* tasks, const double* partial, int ntasks, int nrhs, double* out) {
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int s = warp; s < nrhs; s += nw) {
+    const double v = rhs_partial_sum_warp(tasks, partial, ntasks, s);
+    if ((threadIdx.x & 31) == 0) out[s] = v;
+  }
+}
+
 // ---------------------------------------------------------------- adjoint face gather
 __global__ void face_gather_kernel(const Geo g, const double* __restrict__ lam, double* __restrict__ grad) {
   const long long total = g.nbnd * g.nrhs;
@@ -379,6 +473,21 @@ cudaError_t launch_resid(const ResidArgs& a, double* out, double* inv_bnorm, cud
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   resid_finish_kernel<<<1, 128, 0, s>>>(a.g.nrhs, a.nblk, a.part, out, inv_bnorm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bhat_sq(const Geo& g, const double* f, const double* bnd, double* part, int nblk, double* out,
+                           double* inv_bnorm, cudaStream_t s) {
+  bhat_sq_kernel<<<dim3((unsigned)nblk, (unsigned)g.nrhs), 256, 0, s>>>(g, f, bnd, part, nblk);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  bhat_sq_finish_kernel<<<1, 128, 0, s>>>(g.nrhs, nblk, part, out, inv_bnorm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_task_sums(const Task* tasks, const double* partial, int ntasks, int nrhs, double* out,
+                             cudaStream_t s) {
+  task_sums_kernel<<<1, 256, 0, s>>>(tasks, partial, ntasks, nrhs, out);
   return cudaGetLastError();
 }
 

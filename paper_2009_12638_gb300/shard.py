@@ -304,7 +304,7 @@ def sharded_solve(layout: ShardLayout, shards, comm, bnd=None, f=None, x0=None, 
     def on(dev, t):
         return None if t is None else t.to(dev, dtype=torch.float64).contiguous()
 
-    B, F, XA, XB, BT = [], [], [], [], []
+    B, F, X, BT = [], [], [], []
     for s in shards:
         lx, ly, lz = layout.dims(s.rank)
         bl = layout.local_boundary(s.rank, bnd)
@@ -314,26 +314,50 @@ def sharded_solve(layout: ShardLayout, shards, comm, bnd=None, f=None, x0=None, 
         B.append(BT[-1].clone())                     # plus the neighbours' planes, swapped every sweep
         F.append(on(s.device, layout.local_field(s.rank, f)))
         x = layout.local_field(s.rank, x0)
-        XA.append(on(s.device, x) if x is not None else torch.zeros((nrhs, lz, ly, lx), dtype=torch.float64,
-                                                                    device=s.device))
-        XB.append(torch.empty_like(XA[-1]))
+        x = on(s.device, x) if x is not None else torch.zeros((nrhs, lz, ly, lx), dtype=torch.float64, device=s.device)
+        # three rotating iterates: sweep k reads x^k (buffer k % 3) and writes x^{k+1}
+        # while the stop test of x^{k-1} (the third buffer) is still being read
+        X.append([x, torch.empty_like(x), torch.empty_like(x)])
     # ||bhat||^2 of the global system: f plus the domain-boundary data only
-    bb = comm.allreduce_sum([s.norms(XB[i].zero_(), F[i], BT[i])[1] for i, s in enumerate(shards)])
+    bb = comm.allreduce_sum([s.norms(X[i][1].zero_(), F[i], BT[i])[1] for i, s in enumerate(shards)])
     bnorm = np.sqrt(bb.cpu().numpy())
-    result = [torch.empty_like(x) for x in XA]
+    result = [torch.empty_like(x[0]) for x in X]
     active = np.ones(nrhs, dtype=bool)
     kfinal = np.zeros(nrhs, dtype=np.int64)
     conv = np.zeros(nrhs, dtype=bool)
     hist = []
-    k = 0
-    for k in range(outer_maxit + 1):
-        planes = [s.face_planes(XA[i]) for i, s in enumerate(shards)]
+
+    def launch(k):
+        """Enqueue sweep k (x^k -> x^{k+1}; at k = outer_maxit the residual of x^k
+        only), the sum of the shares over ranks and its copy to the host; returns
+        (host sum, event that completes with the copy or None)."""
+        xk = [X[i][k % 3] for i in range(len(shards))]
+        planes = [s.face_planes(xk[i]) for i, s in enumerate(shards)]
         comm.exchange(shards, planes, B)
         if k < outer_maxit:
-            rr = [s.sweep(XA[i], XB[i], F[i], B[i], sweep_opts) for i, s in enumerate(shards)]
+            rr = [s.sweep(xk[i], X[i][(k + 1) % 3], F[i], B[i], sweep_opts) for i, s in enumerate(shards)]
         else:  # the last allowed iterate: its residual only
-            rr = [s.norms(XA[i], F[i], B[i])[0] for i, s in enumerate(shards)]
-        tot = comm.allreduce_sum(rr).cpu().numpy()
+            rr = [s.norms(xk[i], F[i], B[i])[0] for i, s in enumerate(shards)]
+        tot = comm.allreduce_sum(rr)
+        if not tot.is_cuda:
+            return tot, None
+        host = torch.empty(tot.shape, dtype=tot.dtype, pin_memory=True)
+        host.copy_(tot, non_blocking=True)
+        ev = torch.cuda.Event()
+        ev.record(torch.cuda.current_stream(tot.device))
+        return host, ev
+
+    # The stop test of x^k is read on the host only after sweep k+1 has been
+    # enqueued, so the GPUs never wait for it (one sweep of work past the stop
+    # is discarded).  x^k stays in its buffer until sweep k+2 is enqueued.
+    k = 0
+    pending = launch(0)
+    while True:
+        nxt = launch(k + 1) if k < outer_maxit else None
+        host, ev = pending
+        if ev is not None:
+            ev.synchronize()
+        tot = host.numpy()
         rho = np.where(bnorm > 0.0, np.sqrt(tot) / np.where(bnorm > 0.0, bnorm, 1.0), np.sqrt(tot))
         if history:
             hist.append(rho.copy())
@@ -343,10 +367,11 @@ def sharded_solve(layout: ShardLayout, shards, comm, bnd=None, f=None, x0=None, 
                 active[r] = False
                 kfinal[r] = k
                 for i in range(len(shards)):
-                    result[i][r].copy_(XA[i][r])
+                    result[i][r].copy_(X[i][k % 3][r])
         if not active.any():
             break
-        XA, XB = XB, XA
+        pending = nxt
+        k += 1
     # the true residual of the returned iterates (quiescent: fresh planes, one sum)
     planes = [s.face_planes(result[i]) for i, s in enumerate(shards)]
     comm.exchange(shards, planes, B)
