@@ -220,13 +220,22 @@ class DistComm:
     that face (one send and one receive per neighbour pair and sweep), the
     shares of the squared norms are summed by one all-reduce."""
 
-    def __init__(self, layout: ShardLayout, group=None):
+    def __init__(self, layout: ShardLayout, group=None, stage_on_host=None):
+        """stage_on_host: move device tensors through host memory for the
+        exchange and the sum (default: when the group's backend is gloo, which
+        carries host tensors only -- e.g. several processes sharing a GPU)."""
         import torch.distributed as dist
         self.dist = dist
         self.layout = layout
         self.group = group
         if dist.get_world_size(group) != layout.size:
             raise ValueError(f"the layout has {layout.size} ranks, the process group {dist.get_world_size(group)}")
+        if stage_on_host is None:
+            stage_on_host = dist.get_backend(group) == "gloo"
+        self.stage = bool(stage_on_host)
+
+    def _wire(self, t):
+        return t.cpu() if self.stage and t.is_cuda else t
 
     def exchange(self, shards, planes, bnds):
         dist = self.dist
@@ -239,7 +248,7 @@ class DistComm:
                     continue
                 off, shp = loc[f]
                 n = shp[0] * shp[1]
-                send = planes[i][:, off:off + n].contiguous()
+                send = self._wire(planes[i][:, off:off + n].contiguous())
                 recv = torch.empty_like(send)
                 ops.append(dist.P2POp(dist.isend, send, nb, self.group))
                 ops.append(dist.P2POp(dist.irecv, recv, nb, self.group))
@@ -254,6 +263,7 @@ class DistComm:
         tot = parts[0].clone()
         for p in parts[1:]:
             tot += p
+        tot = self._wire(tot)
         self.dist.all_reduce(tot, op=self.dist.ReduceOp.SUM, group=self.group)
         return tot
 
@@ -384,9 +394,11 @@ def sharded_solve(layout: ShardLayout, shards, comm, bnd=None, f=None, x0=None, 
 
 
 def solve_distributed(nx, ny, nz, cx, cy, cz, ranks, bnd=None, f=None, x0=None, group=None, device=None, **opts):
-    """Convenience entry for one process per GPU under torch.distributed (NCCL):
-    this rank builds its shard of the rank grid ``ranks`` = (rx, ry, rz) and
-    runs ``sharded_solve``.  Returns (this rank's part of x, ShardedStats)."""
+    """Convenience entry for one process per shard under torch.distributed (NCCL
+    between GPUs; gloo works too, through host memory, e.g. for several
+    processes sharing one GPU): this rank builds its shard of the rank grid
+    ``ranks`` = (rx, ry, rz) and runs ``sharded_solve``.  Returns (this rank's
+    part of x, ShardedStats)."""
     import torch.distributed as dist
     layout = ShardLayout(nx, ny, nz, cx, cy, cz, ranks)
     rank = dist.get_rank(group)

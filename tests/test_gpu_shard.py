@@ -138,3 +138,58 @@ def test_local_shards_mixed_match_the_single_grid_solve():
     assert g.residual(x, bnd=b)[0] == pytest.approx(st.rel_residual, rel=1e-6)
     n = cfg["nx"]
     assert (x - x1).abs().max().item() <= 2 * 0.5 * (n + 1) ** 2 * 1e-8 * x1.abs().max().item()
+
+
+# ---------------------------------------------------------------- two processes, torch.distributed
+def _dist_rank(rank, world, port, ranks, out):
+    import os
+
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    torch.cuda.set_device(0)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from paper_2009_12638_gb300.shard import solve_distributed
+        cfg = inputs.make_config("laplace32_linear")
+        n = cfg["nx"]
+        x, st = solve_distributed(n, n, n, cfg["cx"], cfg["cy"], cfg["cz"], ranks, bnd=cuda(cfg["bnd"]),
+                                  precision="fp64", outer_tol=1e-10)
+        out[rank] = (x.cpu().numpy(), st.status, st.outer_its, st.rel_residual)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_processes_solve_distributed_over_gloo(oracle_mod):
+    """solve_distributed end to end with the GPU shards: two processes (one
+    shard each, both on this GPU, exchanging through gloo and host memory --
+    their kernels never wait on one another) give the oracle's solution."""
+    import socket
+
+    import torch.multiprocessing as mp
+    from paper_2009_12638_gb300.shard import ShardLayout
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ranks = (1, 1, 2)
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    procs = [ctx.Process(target=_dist_rank, args=(r, 2, port, ranks, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=600)
+        assert p.exitcode == 0
+    cfg = inputs.make_config("laplace32_linear")
+    n = cfg["nx"]
+    lay = ShardLayout(n, n, n, cfg["cx"], cfg["cy"], cfg["cz"], ranks)
+    x = np.empty((1, n, n, n))
+    for r in range(2):
+        (x0, x1), (y0, y1), (z0, z1) = lay.box(r)
+        x[:, z0:z1, y0:y1, x0:x1] = out[r][0]
+    assert out[0][1:3] == out[1][1:3] and out[0][1] == 0
+    ref = oracle_mod.solve(n, n, n, cfg["cx"], cfg["cy"], cfg["cz"], bnd=cfg["bnd"][0], outer_tol=1e-10)
+    assert abs(out[0][2] - ref["outer_its"]) <= 1
+    assert np.abs(x[0] - ref["x"]).max() <= 1e-9 * np.abs(ref["x"]).max()
+    assert out[0][3] < 1e-10
