@@ -208,7 +208,89 @@ __device__ __forceinline__ void cluster_sum2_f32(float& a, float& b, float* slot
 struct ResRed {
   float eta[kMaxCluster], gam[kMaxCluster];
   float weta[32], wgam[32];
+  // the tagged sum (cluster_sum_tagged_f32): one word per CTA (total bits |
+  // tag << 32), the total handed to the CTA, the tag of the next sum, a flag
+  // set once a wait ran out, and where that is reported
+  unsigned long long tword[kMaxCluster];
+  float ttot;
+  unsigned tseq;
+  int tstale;
+  int* err;
 };
+
+// Set up the tagged-sum state of a kernel's ResRed.  Called by every thread
+// before the kernel's first cluster barrier (no CTA stores a word into another
+// before every CTA has passed it).
+__device__ __forceinline__ void res_red_init(ResRed& rr, int* err) {
+  if (threadIdx.x < kMaxCluster) rr.tword[threadIdx.x] = 0xffffffff00000000ull;  // a tag no sum uses
+  if (threadIdx.x == 0) {
+    rr.tseq = 0u;
+    rr.tstale = 0;
+    rr.err = err;
+  }
+}
+
+constexpr long long kTagPollLimit = 1ll << 22;  // ~0.1 s of polling: far beyond any CG step
+
+// Cluster-wide FP32 sum with the bits of cluster_sum_f32 (the same warp
+// butterflies, the same CTA pre-reduction, the CTA totals added in rank
+// order), without a cluster barrier.  Warp 0 of each CTA stores its CTA
+// total into word [rank] of every CTA as one 64-bit word tagged with this
+// sum's number, polls its own CTA's csize words until every one carries that
+// tag, and hands the total to the CTA's warps through shared memory (so all
+// warps of a CTA always take the same value).  The stores are relaxed: the sum
+// publishes nothing but its own value, so a caller that needs earlier writes
+// visible to other CTAs uses a cluster barrier.  Words are reused, so two
+// tagged sums of a launch must have a cluster barrier between them (no CTA
+// stores the next sum's word before every CTA has read this one's); tags never
+// repeat within a launch.  The wait is bounded: after kTagPollLimit polls the
+// CTA records kErrTimeout, takes the words as they are, and waits in no
+// later tagged sum of the launch.
+template <int NT>
+__device__ __forceinline__ float cluster_sum_tagged_f32(float v, ResRed& rr, unsigned rank, unsigned csize) {
+  constexpr int NW = NT / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) rr.weta[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    const unsigned tag = rr.tseq;
+    float t = lane < NW ? rr.weta[lane] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane < (int)csize) {
+      const unsigned long long w = (unsigned long long)__float_as_uint(t) | ((unsigned long long)tag << 32);
+      asm volatile("st.relaxed.cluster.shared::cluster.b64 [%0], %1;" ::"r"(cl_map(&rr.tword[rank], (unsigned)lane)),
+                   "l"(w)
+                   : "memory");
+    }
+    const unsigned mine = (unsigned)__cvta_generic_to_shared(&rr.tword[lane < (int)csize ? lane : 0]);
+    bool stale = rr.tstale != 0;
+    unsigned long long w = 0ull;
+    for (long long polls = 0;; ++polls) {
+      asm volatile("ld.relaxed.cluster.shared::cta.b64 %0, [%1];" : "=l"(w) : "r"(mine) : "memory");
+      if (stale || __all_sync(0xffffffffu, lane >= (int)csize || (unsigned)(w >> 32) == tag)) break;
+      if (polls >= kTagPollLimit) {
+        stale = true;
+        if (lane == 0) {
+          rr.tstale = 1;
+          atomicOr(rr.err, kErrTimeout);
+        }
+        break;
+      }
+    }
+    float acc = lane < (int)csize ? __uint_as_float((unsigned)w) : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      rr.ttot = acc;
+      rr.tseq = tag + 1u;
+    }
+  }
+  __syncthreads();
+  return rr.ttot;
+}
 
 // Shared memory used by the reductions of one cluster, and the CG scalars
 // that thread 0 derives from them and every thread reads.

@@ -362,7 +362,12 @@ __device__ int resident_cg_two_reductions(float4 (&r4)[KC][ZS], float4 (&d4)[DS 
         c = zp;
       }
     }
-    const float eta = cluster_sum_f32<NT>(eta_loc, rr.eta, rr.weta, rank, csize);
+    // eta needs no cluster barrier: it publishes only its own value (the r
+    // halo pushes of pass B are made visible by the gamma sum's barrier), and
+    // no CTA pushes r into a neighbour before that neighbour's warps have
+    // finished pass C, whose halo reads feed (through p) every eta partial
+    // the neighbour's word carries
+    const float eta = cluster_sum_tagged_f32<NT>(eta_loc, rr, rank, csize);
     if (!(eta > 0.f)) break;  // curvature breakdown or NaN: keep d from earlier steps
     alpha = gamma / eta;
     // ---------------- pass B: (QR = false: d += alpha p,) r -= alpha q, gamma = r.r, push boundary r
