@@ -145,6 +145,11 @@ typedef struct {
   ms_trace_rec* trace;   /* HOST, optional [trace_cap]: per block solve records, written by the kernels
                             into a device ring and copied here after the solve in the order they were
                             taken (when more than trace_cap were taken, the last trace_cap) */
+  int sum_polls;         /* resident engine: polls a CTA may spend in one cluster-wide sum that has no
+                            cluster barrier (each CTA's total arrives as a tagged word) before it gives
+                            up; the solve then ends with MS_ERR_TIMEOUT (ms_sweep: with stats).
+                            0 (default) = 2^22 polls, far beyond any CG step; small values exist to
+                            test that bounded wait */
 } ms_opts;
 
 typedef struct {

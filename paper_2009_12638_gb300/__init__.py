@@ -96,7 +96,7 @@ def _stream_handle(device):
 def _make_opts(lib, mode="sync", precision="mixed", inner_rtol=1e-6, inner_maxit=50, outer_tol=1e-8,
                outer_maxit=100000, time_limit_ms=0.0, cluster=0, threads=0, slots=0, check_every=0, use_graph=True,
                slow_block=-1, slow_ns=0, profile=False, engine="auto", persistent="auto", variant=-1,
-               inner_adapt=False, overlap=0, inner="cg", gmres_restart=10, wait_polls=0):
+               inner_adapt=False, overlap=0, inner="cg", gmres_restart=10, wait_polls=0, sum_polls=0):
     o = _lib.Opts()
     lib.ms_default_opts(ctypes.byref(o))
     o.mode = _lib.MODE[mode] if isinstance(mode, str) else int(mode)
@@ -123,6 +123,7 @@ def _make_opts(lib, mode="sync", precision="mixed", inner_rtol=1e-6, inner_maxit
     o.inner_method = {"cg": 0, "gmres": 1}[inner] if isinstance(inner, str) else int(inner)
     o.gmres_restart = int(gmres_restart)
     o.wait_polls = int(wait_polls)
+    o.sum_polls = int(sum_polls)
     return o
 
 
@@ -215,6 +216,8 @@ class Grid:
         by this many points per face, streaming engine), inner ('cg'|'gmres'),
         gmres_restart (GMRES basis size per cycle, 1..50), wait_polls
         (persistent sync launch: poll budget of its bounded waits, 0 = default),
+        sum_polls (resident engine: polls before a cluster sum without a
+        cluster barrier gives up, 0 = default; for tests of that wait),
         trace (N > 0: keep the last N block-solve records, returned as
         stats.trace, a numpy array of TRACE_DTYPE, with stats.trace_count).
         """

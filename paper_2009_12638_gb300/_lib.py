@@ -70,6 +70,7 @@ class Opts(ctypes.Structure):
         ("wait_polls", ctypes.c_int),
         ("trace_cap", ctypes.c_int),
         ("trace", ctypes.POINTER(TraceRec)),
+        ("sum_polls", ctypes.c_int),
     ]
 
 

@@ -165,6 +165,7 @@ extern "C" void ms_default_opts(ms_opts* o) {
   o->wait_polls = 0;
   o->trace_cap = 0;
   o->trace = nullptr;
+  o->sum_polls = 0;
 }
 
 static std::vector<int> equal_cuts(int n, int p) {
@@ -285,6 +286,7 @@ static int check_opts(ms_grid* g, const ms_opts& o) {
   if (o.overlap < 0) return fail(g, MS_ERR_ARG, "opts.overlap must be >= 0");
   if (o.wait_polls < 0) return fail(g, MS_ERR_ARG, "opts.wait_polls must be >= 0 (0 = default)");
   if (o.trace_cap < 0) return fail(g, MS_ERR_ARG, "opts.trace_cap must be >= 0");
+  if (o.sum_polls < 0) return fail(g, MS_ERR_ARG, "opts.sum_polls must be >= 0 (0 = default)");
   if (o.inner_method != 0 && o.inner_method != 1) return fail(g, MS_ERR_ARG, "opts.inner_method must be 0 (CG) or 1 (GMRES)");
   if (o.inner_method == 1 && (o.gmres_restart < 1 || o.gmres_restart > kGmresMaxRestart))
     return fail(g, MS_ERR_ARG, "opts.gmres_restart must be 1..%d", kGmresMaxRestart);
@@ -543,8 +545,9 @@ extern "C" int ms_sweep(ms_grid* g, const double* f, const double* bnd, const do
   sa.inner_method = o.inner_method;
   sa.gmres_restart = o.gmres_restart;
   sa.tr = TraceArgs{nullptr, nullptr, 0};
+  sa.sum_polls = o.sum_polls;
   if (shape.variant >= 0) MS_CUDA(g, launch_res_sweep(shape.variant, shape.cluster, shape.slots, shape.smem, sa, stream));
-  else if (shape.variant == -2) MS_CUDA(g, launch_strip_sweep(shape.threads, shape.cluster, shape.slots, sa, stream));
+  else if (shape.variant == -2) MS_CUDA(g, launch_strip_sweep(prec, shape.threads, shape.cluster, shape.slots, sa, stream));
   else MS_CUDA(g, launch_sweep(prec, shape.threads, shape.cluster, shape.slots, sa, stream));
   // the residual share of x^k: the sweep's block partials (owned points), in fixed order
   MS_CUDA(g, launch_task_sums(sa.tasks, sa.partial, ntasks, g->nrhs, rr_dev, stream));
@@ -593,6 +596,10 @@ extern "C" int ms_sweep(ms_grid* g, const double* f, const double* bnd, const do
   st->engine = shape.variant >= 0 ? 2 : 1;
   st->variant = shape.variant;
   st->inner_rtol_final = o.inner_rtol;
+  if (herr & kErrTimeout) {  // a bounded wait of the sweep ran out: its result is not to be used
+    st->status = MS_ERR_TIMEOUT;
+    return fail(g, MS_ERR_TIMEOUT, "ms_sweep: a bounded device wait ran out (device error word 0x%x)", herr);
+  }
   return MS_OK;
 }
 
@@ -948,6 +955,7 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
     sa.ntasks = ntasks;
     sa.counter = &ctl->counter;
     sa.rhs_state = rhs_state;
+    sa.sum_polls = o.sum_polls;
     sa.all_done = &ctl->all_done;
     sa.partial = g->partial.as<double>();
     sa.scratch = g->scratch.p;
@@ -1024,7 +1032,7 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
       for (auto& e : tev) MS_CUDA(g, cudaEventCreate(&e));
       auto sweep_with = [&](const LaunchShape& sh) -> cudaError_t {
         if (sh.variant >= 0) return launch_res_sweep(sh.variant, sh.cluster, sh.slots, sh.smem, sa, stream);
-        if (sh.variant == -2) return launch_strip_sweep(sh.threads, sh.cluster, sh.slots, sa, stream);
+        if (sh.variant == -2) return launch_strip_sweep(prec, sh.threads, sh.cluster, sh.slots, sa, stream);
         return launch_sweep(prec, sh.threads, sh.cluster, sh.slots, sa, stream);
       };
       MS_CUDA(g, sweep_with(cands[0]));
@@ -1042,6 +1050,7 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
       MS_CUDA(g, cudaMemcpyAsync(h_flags + 1, &ctl->err, sizeof(int), cudaMemcpyDeviceToHost, stream));
       MS_CUDA(g, cudaStreamSynchronize(stream));
       if (h_flags[1] & kErrGeometry) return fail(g, MS_ERR_CUDA, "ms_solve: device error word 0x%x", h_flags[1]);
+      if (h_flags[1] & kErrTimeout) status = MS_ERR_TIMEOUT;  // the time limit ran out during the tuning sweeps
       float best_t = 1e30f;
       const bool verbose = std::getenv("MS_TUNE_VERBOSE") != nullptr;
       for (size_t i = 0; i < nc; ++i) {
@@ -1069,7 +1078,7 @@ static int solve_device(ms_grid* g, const double* f, const double* bnd, double* 
     }
     auto sweep_launch = [&](const LaunchShape& sh, cudaStream_t cs) -> cudaError_t {
       if (sh.variant >= 0) return launch_res_sweep(sh.variant, sh.cluster, sh.slots, sh.smem, sa, cs);
-      if (sh.variant == -2) return launch_strip_sweep(sh.threads, sh.cluster, sh.slots, sa, cs);
+      if (sh.variant == -2) return launch_strip_sweep(prec, sh.threads, sh.cluster, sh.slots, sa, cs);
       return launch_sweep(prec, sh.threads, sh.cluster, sh.slots, sa, cs);
     };
     // Persistent dataflow launch or per-sweep graph.  In auto mode the
@@ -1421,6 +1430,7 @@ int solve_async(ms_grid* g, const double* f, const double* bnd, double* x, const
   unsigned long long* inner = reinterpret_cast<unsigned long long*>(ctlb + L.off_inner);
 
   AsyncArgs a;
+  a.sum_polls = o.sum_polls;
   a.g = g->geo();
   a.f = f;
   a.bnd = bnd;

@@ -151,6 +151,30 @@ __device__ __forceinline__ float cluster_sum_f32(float v, float* slots, float* w
   return acc;
 }
 
+// cluster_sum_f32 in FP64 (same tree, same slot rules; slots[kMaxCluster] and
+// wsum[32] of doubles).
+template <int NT>
+__device__ __forceinline__ double cluster_sum_f64(double v, double* slots, double* wsum, unsigned rank,
+                                                  unsigned csize) {
+  constexpr int NW = NT / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) wsum[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    double t = lane < NW ? wsum[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane < (int)csize) cl_store(&slots[rank], (unsigned)lane, t);
+  }
+  cl_barrier();
+  double acc = lane < (int)csize ? slots[lane] : 0.0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  return acc;
+}
+
 // The two halves of cl_barrier(), for work in between: every thread of the
 // cluster arrives (release: its earlier global and shared writes, DSMEM
 // stores included, become visible to the cluster) and later waits (acquire)
@@ -216,21 +240,23 @@ struct ResRed {
   unsigned tseq;
   int tstale;
   int* err;
+  long long tlimit;  // polls before a wait gives up
 };
 
-// Set up the tagged-sum state of a kernel's ResRed.  Called by every thread
-// before the kernel's first cluster barrier (no CTA stores a word into another
-// before every CTA has passed it).
-__device__ __forceinline__ void res_red_init(ResRed& rr, int* err) {
+constexpr long long kTagPollLimit = 1ll << 22;  // ~0.1 s of polling: far beyond any CG step
+
+// Set up the tagged-sum state of a kernel's ResRed (polls: the wait limit, 0 =
+// kTagPollLimit).  Called by every thread before the kernel's first cluster
+// barrier (no CTA stores a word into another before every CTA has passed it).
+__device__ __forceinline__ void res_red_init(ResRed& rr, int* err, long long polls) {
   if (threadIdx.x < kMaxCluster) rr.tword[threadIdx.x] = 0xffffffff00000000ull;  // a tag no sum uses
   if (threadIdx.x == 0) {
     rr.tseq = 0u;
     rr.tstale = 0;
     rr.err = err;
+    rr.tlimit = polls > 0 ? polls : kTagPollLimit;
   }
 }
-
-constexpr long long kTagPollLimit = 1ll << 22;  // ~0.1 s of polling: far beyond any CG step
 
 // Cluster-wide FP32 sum with the bits of cluster_sum_f32 (the same warp
 // butterflies, the same CTA pre-reduction, the CTA totals added in rank
@@ -243,9 +269,10 @@ constexpr long long kTagPollLimit = 1ll << 22;  // ~0.1 s of polling: far beyond
 // visible to other CTAs uses a cluster barrier.  Words are reused, so two
 // tagged sums of a launch must have a cluster barrier between them (no CTA
 // stores the next sum's word before every CTA has read this one's); tags never
-// repeat within a launch.  The wait is bounded: after kTagPollLimit polls the
-// CTA records kErrTimeout, takes the words as they are, and waits in no
-// later tagged sum of the launch.
+// repeat within a launch.  The wait is bounded: after rr.tlimit polls the CTA
+// records kErrTimeout, takes the words as they are, and waits in no later
+// tagged sum of the launch.  Callers keep their control flow independent of
+// a total that may then differ between CTAs (see the CG's breakdown test).
 template <int NT>
 __device__ __forceinline__ float cluster_sum_tagged_f32(float v, ResRed& rr, unsigned rank, unsigned csize) {
   constexpr int NW = NT / 32;
@@ -271,7 +298,7 @@ __device__ __forceinline__ float cluster_sum_tagged_f32(float v, ResRed& rr, uns
     for (long long polls = 0;; ++polls) {
       asm volatile("ld.relaxed.cluster.shared::cta.b64 %0, [%1];" : "=l"(w) : "r"(mine) : "memory");
       if (stale || __all_sync(0xffffffffu, lane >= (int)csize || (unsigned)(w >> 32) == tag)) break;
-      if (polls >= kTagPollLimit) {
+      if (polls >= rr.tlimit) {
         stale = true;
         if (lane == 0) {
           rr.tstale = 1;

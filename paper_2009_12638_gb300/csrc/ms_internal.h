@@ -80,6 +80,7 @@ struct SweepArgs {
   int inner_method;              // 0 CG, 1 restarted GMRES (scalar streaming engine)
   int gmres_restart;             // GMRES basis size per cycle (slot holds gmres_restart + 3 vectors)
   TraceArgs tr;                  // solve trace (rec == nullptr: none)
+  long long sum_polls = 0;       // polls of a tagged cluster sum before it gives up (0 = default)
 };
 
 __host__ __device__ inline double sweep_inner_rtol(const SweepArgs& a, int rhs) {
@@ -193,6 +194,7 @@ struct AsyncArgs {
   unsigned long long slice_ns;        // the launch returns (no error) after this long; the host relaunches
   int* err;
   TraceArgs tr;                       // solve trace (rec == nullptr: none)
+  long long sum_polls = 0;            // polls of a tagged cluster sum before it gives up (0 = default)
 };
 
 struct ResidArgs {
@@ -264,8 +266,8 @@ cudaError_t launch_res_flow(int variant, int cluster, int slots, size_t smem_byt
                             cudaStream_t s);
 cudaError_t res_flow_max_clusters(int variant, int cluster, size_t smem_bytes, int* out);
 // vectorised FP32 streaming engine, sync mode (ms_stream4.cu)
-cudaError_t strip_max_clusters(int threads, int cluster, int* out);
-cudaError_t launch_strip_sweep(int threads, int cluster, int slots, const SweepArgs& a, cudaStream_t s);
+cudaError_t strip_max_clusters(int prec, int threads, int cluster, int* out);  // prec 1 mixed, 0 FP64
+cudaError_t launch_strip_sweep(int prec, int threads, int cluster, int slots, const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_res_sweep(int variant, int cluster, int slots, size_t smem_bytes, const SweepArgs& a,
                              cudaStream_t s);
 

@@ -298,6 +298,7 @@ __device__ int resident_cg_two_reductions(float4 (&r4)[KC][ZS], float4 (&d4)[DS 
   float gamma = gamma0, beta = 0.f, alpha = 0.f;
   float4 q4[QR ? KC : 1][QR ? ZS : 1];
   int m = 0;
+  float gnew = 0.f;
   // d = alpha p + d on one strip-plane (d = alpha p when first == true)
   auto add_d = [&](int k, int z, float4 p, bool first) {
     if constexpr (DS) {
@@ -368,8 +369,16 @@ __device__ int resident_cg_two_reductions(float4 (&r4)[KC][ZS], float4 (&d4)[DS 
     // finished pass C, whose halo reads feed (through p) every eta partial
     // the neighbour's word carries
     const float eta = cluster_sum_tagged_f32<NT>(eta_loc, rr, rank, csize);
-    if (!(eta > 0.f)) break;  // curvature breakdown or NaN: keep d from earlier steps
-    alpha = gamma / eta;
+    // curvature breakdown or NaN: the solve stops with d from the earlier
+    // steps.  No CTA leaves on this total: once a tagged wait ran out anywhere,
+    // CTAs may hold different totals (a CTA that ran on with a wrong alpha
+    // sends wrong partials), and a CTA that left early could end its launch
+    // while the others still push halo data into its shared memory.  The exit
+    // is taken at the gamma sum below, whose cluster barrier gives every CTA
+    // the same total: this CTA runs pass B with alpha = 0 (r and d unchanged)
+    // and contributes NaN, and every CTA leaves after that sum
+    const bool brk = !(eta > 0.f);
+    alpha = brk ? 0.f : gamma / eta;
     // ---------------- pass B: (QR = false: d += alpha p,) r -= alpha q, gamma = r.r, push boundary r
     float g_loc = 0.f;
 #pragma unroll
@@ -404,12 +413,18 @@ __device__ int resident_cg_two_reductions(float4 (&r4)[KC][ZS], float4 (&d4)[DS 
         }
       }
     }
-    pending = QR;
-    const float gnew = cluster_sum_f32<NT>(g_loc, rr.gam, rr.wgam, rank, csize);
+    pending = QR && !brk;
+    gnew = cluster_sum_f32<NT>(brk ? __uint_as_float(0x7fc00000u) : g_loc, rr.gam, rr.wgam, rank, csize);
     m += 1;
-    if (sqrtf(gnew) <= stop || m >= inner_maxit) break;
+    // (NaN: a breakdown in some CTA, not counted below; for any other value the
+    // test is sqrt(gnew) <= stop)
+    if (!(sqrtf(gnew) > stop) || m >= inner_maxit) break;
     beta = gnew / gamma;
     gamma = gnew;
+  }
+  if ((__float_as_uint(gnew) & 0x7fffffffu) > 0x7f800000u) {  // left at a breakdown: that step does not count
+    m -= 1;
+    pending = false;
   }
   if constexpr (QR) {
     // the last d += alpha p (own strips only: p was written by this thread)

@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(NT, 1) res_sweep_kernel(const SweepArgs a, int
   __shared__ ResRed rred;
   __shared__ int s_task[2];
   if (*a.all_done) return;
-  res_red_init(rred, a.err);
+  res_red_init(rred, a.err, a.sum_polls);
   const unsigned rank = cl_rank(), csize = cl_size();
   const int tid = threadIdx.x;
   const int k = *a.k_dev;
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(NT, 1) res_async_kernel(const AsyncArgs a, int
   const Geo G = a.g;
   const long long nxy = (long long)G.nx * G.ny;
   __shared__ unsigned snap[12];
-  res_red_init(rred, a.err);
+  res_red_init(rred, a.err, a.sum_polls);
   AsyncCtl c = async_ctl_init(a, cid, ncl, snap);
   zero_smem<NT>(dyn4, smem_f4);
   for (;; c.par ^= 1) {
@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(NT, 1) res_flow_kernel(const FlowArgs fa, int 
   const Geo G = a.g;
   const long long nxy = (long long)G.nx * G.ny;
   if (tid < 32) wait_budget[tid] = fa.spin_limit;
-  res_red_init(rred, a.err);
+  res_red_init(rred, a.err, a.sum_polls);
   zero_smem<NT>(dyn4, smem_f4);
   int par = 0;
   for (;; par ^= 1) {

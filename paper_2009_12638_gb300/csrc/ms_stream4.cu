@@ -1,6 +1,7 @@
-// ms_stream4.cu -- streaming engine, FP32, vectorised: the inner CG of one
-// block per thread-block cluster with the CG vectors in the cluster's global
-// scratch slot (L2-resident), for blocks too large to keep on chip.
+// ms_stream4.cu -- streaming engine, vectorised, FP32 (mixed precision) or
+// FP64: the inner CG of one block per thread-block cluster with the CG
+// vectors in the cluster's global scratch slot (L2-resident), for blocks too
+// large to keep on chip.
 //
 // Same method and pass structure as block_cg (ms_cg.cuh) -- pass A forms
 // p_new = r + beta p_old on the fly at the point and its neighbours, applies
@@ -22,7 +23,7 @@ namespace {
 
 struct StripGeo {
   int bx, by, bz, spr, pitch, plane, nstrips, z0, z1;
-  unsigned magic;  // st / spr == __umulhi(st, magic)
+  unsigned magic;  // st / spr == __umulhi(st, magic) when magic != 0, else exact division
 };
 
 __device__ __forceinline__ StripGeo strip_geo(int bx, int by, int bz, unsigned rank, unsigned csize) {
@@ -36,7 +37,13 @@ __device__ __forceinline__ StripGeo strip_geo(int bx, int by, int bz, unsigned r
   g.nstrips = g.spr * by;
   g.z0 = (int)(((long long)bz * rank) / csize);
   g.z1 = (int)(((long long)bz * (rank + 1)) / csize);
-  g.magic = (unsigned)((0x100000000ULL + (unsigned long long)g.spr - 1) / (unsigned long long)g.spr);
+  // ceil(2^32 / spr) divides exactly while st * spr < 2^32 for every strip id
+  // st < nstrips; spr = 1 (the multiplier would be 2^32) and larger planes
+  // divide directly
+  const unsigned long long m = (0x100000000ULL + (unsigned long long)g.spr - 1) / (unsigned long long)g.spr;
+  g.magic = (m <= 0xFFFFFFFFULL && (unsigned long long)g.nstrips * (unsigned long long)g.spr < 0x100000000ULL)
+                ? (unsigned)m
+                : 0u;
   return g;
 }
 
@@ -64,7 +71,7 @@ __device__ __forceinline__ StripPos strip_pos(const StripGeo& g, int st, int lan
   StripPos s;
   s.has = st < g.nstrips;
   const int stc = s.has ? st : 0;
-  s.y = (int)__umulhi((unsigned)stc, g.magic);
+  s.y = g.magic ? (int)__umulhi((unsigned)stc, g.magic) : stc / g.spr;
   s.xs = stc - s.y * g.spr;
   s.off = s.y * g.pitch + 4 * s.xs;
   const int rem = g.bx - 4 * s.xs;
@@ -86,68 +93,134 @@ __device__ __forceinline__ float4 stencil_strip(float4 c, float4 zm, float4 zp, 
   return q;
 }
 
+// The FP64 strip: 4 doubles (32 bytes), moved as two 16-byte accesses.
+struct __align__(16) dbl4 {
+  double x, y, z, w;
+};
+__device__ __forceinline__ dbl4 ld4(const double* p) {
+  const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+  return dbl4{a.x, a.y, b.x, b.y};
+}
+__device__ __forceinline__ void st4(double* p, dbl4 v) {
+  *reinterpret_cast<double2*>(p) = make_double2(v.x, v.y);
+  *reinterpret_cast<double2*>(p + 2) = make_double2(v.z, v.w);
+}
+__device__ __forceinline__ dbl4 fma4(double a, dbl4 x, dbl4 y) {
+  return dbl4{fma(a, x.x, y.x), fma(a, x.y, y.y), fma(a, x.z, y.z), fma(a, x.w, y.w)};
+}
+__device__ __forceinline__ dbl4 msk4(dbl4 v, unsigned m) {
+  return dbl4{(m & 1u) ? v.x : 0.0, (m & 2u) ? v.y : 0.0, (m & 4u) ? v.z : 0.0, (m & 8u) ? v.w : 0.0};
+}
+__device__ __forceinline__ double dot4f(dbl4 a, dbl4 b) { return (a.x * b.x + a.y * b.y) + (a.z * b.z + a.w * b.w); }
+__device__ __forceinline__ dbl4 stencil_strip(dbl4 c, dbl4 zm, dbl4 zp, dbl4 ym, dbl4 yp, double xl, double xr) {
+  dbl4 q;
+  q.x = 6.0 * c.x - (((xl + c.y) + (ym.x + yp.x)) + (zm.x + zp.x));
+  q.y = 6.0 * c.y - (((c.x + c.z) + (ym.y + yp.y)) + (zm.y + zp.y));
+  q.z = 6.0 * c.z - (((c.y + c.w) + (ym.z + yp.z)) + (zm.z + zp.z));
+  q.w = 6.0 * c.w - (((c.z + xr) + (ym.w + yp.w)) + (zm.w + zp.w));
+  return q;
+}
+
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+
+template <typename T>
+struct StripT;  // the strip type of a precision
+template <>
+struct StripT<float> {
+  using V = float4;
+  __device__ static V zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+  __device__ static V make(const float (&v)[4]) { return make_float4(v[0], v[1], v[2], v[3]); }
+};
+template <>
+struct StripT<double> {
+  using V = dbl4;
+  __device__ static V zero() { return dbl4{0.0, 0.0, 0.0, 0.0}; }
+  __device__ static V make(const double (&v)[4]) { return dbl4{v[0], v[1], v[2], v[3]}; }
+};
+
+// The two cluster sums of a CG iteration (which = 0: p.q, 1: r.r) in the
+// precision of the inner solve, on the reduction slots of that precision.
+template <int NT>
+__device__ __forceinline__ float strip_sum(float v, int which, ResRed& rr, RedSmem&, unsigned rank, unsigned csize) {
+  return which ? cluster_sum_f32<NT>(v, rr.gam, rr.wgam, rank, csize)
+               : cluster_sum_f32<NT>(v, rr.eta, rr.weta, rank, csize);
+}
+template <int NT>
+__device__ __forceinline__ double strip_sum(double v, int which, ResRed&, RedSmem& sm, unsigned rank,
+                                            unsigned csize) {
+  return cluster_sum_f64<NT>(v, sm.slots[1 + which][0], sm.wsum[which], rank, csize);
+}
+
 }  // namespace
 
-constexpr int kStripsInFlight = 2;  // strip columns a thread marches up z together
+// strip columns a thread marches up z together (FP64 strips take twice the
+// registers: one column)
+template <typename T>
+constexpr int kStripsInFlight = sizeof(T) == 4 ? 2 : 1;
 
 // The inner CG on the strip layout.  Vectors r, p0, p1, d of the slot use the
 // pitch-padded layout (z, y, 4*xs + lane); r holds the residual on entry
 // (padding lanes zero), gamma0 = r.r reduced.  Returns m; d holds the
-// correction when m > 0.  The two sums of an iteration are FP32 cluster sums
-// pre-reduced inside each CTA (cluster_sum_f32), and every thread forms the
-// same FP32 scalars alpha, beta and the stop test from them (no broadcast).
-template <int NT>
-__device__ int strip_cg(const CgVecs<float>& v, const StripGeo& g, float gamma0, float inner_rtol, int inner_maxit,
-                        ResRed& rr, unsigned rank, unsigned csize) {
-  if (!(gamma0 > 0.f) || inner_maxit <= 0) return 0;
+// correction when m > 0.  T is the inner precision (float: the mixed-
+// precision solve, double: the plain FP64 one).  The two sums of an
+// iteration are cluster sums in T pre-reduced inside each CTA, and every
+// thread forms the same scalars alpha, beta and the stop test from them (no
+// broadcast).
+template <int NT, typename T>
+__device__ int strip_cg(const CgVecs<T>& v, const StripGeo& g, T gamma0, T inner_rtol, int inner_maxit, ResRed& rr,
+                        RedSmem& sm, unsigned rank, unsigned csize) {
+  using V = typename StripT<T>::V;
+  constexpr int SF = kStripsInFlight<T>;
+  if (!(gamma0 > T(0)) || inner_maxit <= 0) return 0;
   const int lane = threadIdx.x & 31;
   const int wbase = threadIdx.x - lane;
-  const float stop = inner_rtol * sqrtf(gamma0);
-  float gamma = gamma0, beta = 0.f;
+  const T stop = inner_rtol * sqrt(gamma0);
+  T gamma = gamma0, beta = T(0);
   int m = 0;
-  float* po = v.p0;
-  float* pn = v.p1;
+  T* po = v.p0;
+  T* pn = v.p1;
   bool first = true;
   for (;;) {
     // ---------------- pass A: p_new at the strip and its neighbours, q = A_ii p_new, eta = p.q
     // (within a pass the vectors are distinct: pass A reads r and p_old and writes
     // p_new, so the next planes' loads may move ahead of this plane's store).
-    // Each thread marches kStripsInFlight strip columns up z together, so twice
-    // as many independent loads are in flight per plane step.
-    const float* __restrict__ rA = v.r;
-    const float* __restrict__ poA = po;
-    float* __restrict__ pnA = pn;
-    auto pnew = [&](long long i) -> float4 {  // i: float index of a strip start
-      const float4 r = ld4(rA + i);
+    // Each thread marches SF strip columns up z together (FP32: 2), so that
+    // many independent loads are in flight per plane step.
+    const T* __restrict__ rA = v.r;
+    const T* __restrict__ poA = po;
+    T* __restrict__ pnA = pn;
+    auto pnew = [&](long long i) -> V {  // i: element index of a strip start
+      const V r = ld4(rA + i);
       return first ? r : fma4(beta, ld4(poA + i), r);
     };
-    auto pnew_s = [&](long long i) -> float { return first ? rA[i] : fmaf(beta, poA[i], rA[i]); };
-    float eta_loc = 0.f;
-    for (int s0 = wbase; s0 < g.nstrips; s0 += kStripsInFlight * NT) {
-      StripPos s[kStripsInFlight];
-      float4 zm[kStripsInFlight], c[kStripsInFlight];
+    auto pnew_s = [&](long long i) -> T { return first ? rA[i] : fma_t(beta, poA[i], rA[i]); };
+    T eta_loc = T(0);
+    for (int s0 = wbase; s0 < g.nstrips; s0 += SF * NT) {
+      StripPos s[SF];
+      V zm[SF], c[SF];
 #pragma unroll
-      for (int u = 0; u < kStripsInFlight; ++u) {
+      for (int u = 0; u < SF; ++u) {
         s[u] = strip_pos(g, s0 + u * NT + lane, lane);
-        zm[u] = (s[u].has && g.z0 > 0 && g.z0 < g.z1) ? pnew((long long)(g.z0 - 1) * g.plane + s[u].off) : zero4();
-        c[u] = (s[u].has && g.z0 < g.z1) ? pnew((long long)g.z0 * g.plane + s[u].off) : zero4();
+        zm[u] = (s[u].has && g.z0 > 0 && g.z0 < g.z1) ? pnew((long long)(g.z0 - 1) * g.plane + s[u].off) : StripT<T>::zero();
+        c[u] = (s[u].has && g.z0 < g.z1) ? pnew((long long)g.z0 * g.plane + s[u].off) : StripT<T>::zero();
       }
       for (int z = g.z0; z < g.z1; ++z) {
         const long long base = (long long)z * g.plane;
-        float4 zp[kStripsInFlight], ym[kStripsInFlight], yp[kStripsInFlight];
+        V zp[SF], ym[SF], yp[SF];
 #pragma unroll
-        for (int u = 0; u < kStripsInFlight; ++u) {
-          zp[u] = (s[u].has && z + 1 < g.bz) ? pnew(base + g.plane + s[u].off) : zero4();
-          ym[u] = (s[u].has && s[u].y > 0) ? pnew(base + s[u].off - g.pitch) : zero4();
-          yp[u] = (s[u].has && s[u].y + 1 < g.by) ? pnew(base + s[u].off + g.pitch) : zero4();
+        for (int u = 0; u < SF; ++u) {
+          zp[u] = (s[u].has && z + 1 < g.bz) ? pnew(base + g.plane + s[u].off) : StripT<T>::zero();
+          ym[u] = (s[u].has && s[u].y > 0) ? pnew(base + s[u].off - g.pitch) : StripT<T>::zero();
+          yp[u] = (s[u].has && s[u].y + 1 < g.by) ? pnew(base + s[u].off + g.pitch) : StripT<T>::zero();
         }
 #pragma unroll
-        for (int u = 0; u < kStripsInFlight; ++u) {
-          const float l_sh = __shfl_up_sync(0xffffffffu, c[u].w, 1);
-          const float r_sh = __shfl_down_sync(0xffffffffu, c[u].x, 1);
-          const float xl = s[u].lin ? l_sh : ((s[u].has && s[u].xs > 0) ? pnew_s(base + s[u].off - 1) : 0.f);
-          const float xr = s[u].rin ? r_sh : ((s[u].has && s[u].xs + 1 < g.spr) ? pnew_s(base + s[u].off + 4) : 0.f);
-          const float4 q = msk4(stencil_strip(c[u], zm[u], zp[u], ym[u], yp[u], xl, xr), s[u].msk);
+        for (int u = 0; u < SF; ++u) {
+          const T l_sh = __shfl_up_sync(0xffffffffu, c[u].w, 1);
+          const T r_sh = __shfl_down_sync(0xffffffffu, c[u].x, 1);
+          const T xl = s[u].lin ? l_sh : ((s[u].has && s[u].xs > 0) ? pnew_s(base + s[u].off - 1) : T(0));
+          const T xr = s[u].rin ? r_sh : ((s[u].has && s[u].xs + 1 < g.spr) ? pnew_s(base + s[u].off + 4) : T(0));
+          const V q = msk4(stencil_strip(c[u], zm[u], zp[u], ym[u], yp[u], xl, xr), s[u].msk);
           if (s[u].has) st4(pnA + base + s[u].off, c[u]);
           eta_loc += dot4f(c[u], q);
           zm[u] = c[u];
@@ -155,48 +228,48 @@ __device__ int strip_cg(const CgVecs<float>& v, const StripGeo& g, float gamma0,
         }
       }
     }
-    const float eta = cluster_sum_f32<NT>(eta_loc, rr.eta, rr.weta, rank, csize);
-    if (!(eta > 0.f)) break;  // curvature breakdown or NaN: keep d from earlier steps
-    const float alpha = gamma / eta;
+    const T eta = strip_sum<NT>(eta_loc, 0, rr, sm, rank, csize);
+    if (!(eta > T(0))) break;  // curvature breakdown or NaN: keep d from earlier steps
+    const T alpha = gamma / eta;
     // ---------------- pass B: q = A_ii p_new again, d += alpha p, r -= alpha q, gamma = r.r
     // (reads p_new; d and r are read and written at the strip itself only)
-    const float* __restrict__ pnB = pn;
-    float* __restrict__ dB = v.d;
-    float* __restrict__ rB = v.r;
-    float g_loc = 0.f;
-    for (int s0 = wbase; s0 < g.nstrips; s0 += kStripsInFlight * NT) {
-      StripPos s[kStripsInFlight];
-      float4 zm[kStripsInFlight], c[kStripsInFlight];
+    const T* __restrict__ pnB = pn;
+    T* __restrict__ dB = v.d;
+    T* __restrict__ rB = v.r;
+    T g_loc = T(0);
+    for (int s0 = wbase; s0 < g.nstrips; s0 += SF * NT) {
+      StripPos s[SF];
+      V zm[SF], c[SF];
 #pragma unroll
-      for (int u = 0; u < kStripsInFlight; ++u) {
+      for (int u = 0; u < SF; ++u) {
         s[u] = strip_pos(g, s0 + u * NT + lane, lane);
-        zm[u] = (s[u].has && g.z0 > 0 && g.z0 < g.z1) ? ld4(pnB + (long long)(g.z0 - 1) * g.plane + s[u].off) : zero4();
-        c[u] = (s[u].has && g.z0 < g.z1) ? ld4(pnB + (long long)g.z0 * g.plane + s[u].off) : zero4();
+        zm[u] = (s[u].has && g.z0 > 0 && g.z0 < g.z1) ? ld4(pnB + (long long)(g.z0 - 1) * g.plane + s[u].off) : StripT<T>::zero();
+        c[u] = (s[u].has && g.z0 < g.z1) ? ld4(pnB + (long long)g.z0 * g.plane + s[u].off) : StripT<T>::zero();
       }
       for (int z = g.z0; z < g.z1; ++z) {
         const long long base = (long long)z * g.plane;
-        float4 zp[kStripsInFlight], ym[kStripsInFlight], yp[kStripsInFlight], dd[kStripsInFlight],
-            ro[kStripsInFlight];
+        V zp[SF], ym[SF], yp[SF], dd[SF],
+            ro[SF];
 #pragma unroll
-        for (int u = 0; u < kStripsInFlight; ++u) {
+        for (int u = 0; u < SF; ++u) {
           const long long i = base + s[u].off;
-          zp[u] = (s[u].has && z + 1 < g.bz) ? ld4(pnB + i + g.plane) : zero4();
-          ym[u] = (s[u].has && s[u].y > 0) ? ld4(pnB + i - g.pitch) : zero4();
-          yp[u] = (s[u].has && s[u].y + 1 < g.by) ? ld4(pnB + i + g.pitch) : zero4();
-          dd[u] = (s[u].has && !first) ? ld4(dB + i) : zero4();
-          ro[u] = s[u].has ? ld4(rB + i) : zero4();
+          zp[u] = (s[u].has && z + 1 < g.bz) ? ld4(pnB + i + g.plane) : StripT<T>::zero();
+          ym[u] = (s[u].has && s[u].y > 0) ? ld4(pnB + i - g.pitch) : StripT<T>::zero();
+          yp[u] = (s[u].has && s[u].y + 1 < g.by) ? ld4(pnB + i + g.pitch) : StripT<T>::zero();
+          dd[u] = (s[u].has && !first) ? ld4(dB + i) : StripT<T>::zero();
+          ro[u] = s[u].has ? ld4(rB + i) : StripT<T>::zero();
         }
 #pragma unroll
-        for (int u = 0; u < kStripsInFlight; ++u) {
+        for (int u = 0; u < SF; ++u) {
           const long long i = base + s[u].off;
-          const float l_sh = __shfl_up_sync(0xffffffffu, c[u].w, 1);
-          const float r_sh = __shfl_down_sync(0xffffffffu, c[u].x, 1);
-          const float xl = s[u].lin ? l_sh : ((s[u].has && s[u].xs > 0) ? pnB[i - 1] : 0.f);
-          const float xr = s[u].rin ? r_sh : ((s[u].has && s[u].xs + 1 < g.spr) ? pnB[i + 4] : 0.f);
-          const float4 q = msk4(stencil_strip(c[u], zm[u], zp[u], ym[u], yp[u], xl, xr), s[u].msk);
+          const T l_sh = __shfl_up_sync(0xffffffffu, c[u].w, 1);
+          const T r_sh = __shfl_down_sync(0xffffffffu, c[u].x, 1);
+          const T xl = s[u].lin ? l_sh : ((s[u].has && s[u].xs > 0) ? pnB[i - 1] : T(0));
+          const T xr = s[u].rin ? r_sh : ((s[u].has && s[u].xs + 1 < g.spr) ? pnB[i + 4] : T(0));
+          const V q = msk4(stencil_strip(c[u], zm[u], zp[u], ym[u], yp[u], xl, xr), s[u].msk);
           if (s[u].has) {
             st4(dB + i, fma4(alpha, c[u], dd[u]));
-            const float4 r = fma4(-alpha, q, ro[u]);
+            const V r = fma4(-alpha, q, ro[u]);
             st4(rB + i, r);
             g_loc += dot4f(r, r);
           }
@@ -205,13 +278,13 @@ __device__ int strip_cg(const CgVecs<float>& v, const StripGeo& g, float gamma0,
         }
       }
     }
-    const float gnew = cluster_sum_f32<NT>(g_loc, rr.gam, rr.wgam, rank, csize);
+    const T gnew = strip_sum<NT>(g_loc, 1, rr, sm, rank, csize);
     m += 1;
-    if (sqrtf(gnew) <= stop || m >= inner_maxit) break;
+    if (sqrt(gnew) <= stop || m >= inner_maxit) break;
     beta = gnew / gamma;
     gamma = gnew;
     first = false;
-    float* tp = po;
+    T* tp = po;
     po = pn;
     pn = tp;
   }
@@ -219,9 +292,10 @@ __device__ int strip_cg(const CgVecs<float>& v, const StripGeo& g, float gamma0,
 }
 
 // One synchronous outer sweep with the vectorised streaming CG (contract of
-// sweep_kernel in ms_kernels.cu; mixed precision only).
-template <int NT>
+// sweep_kernel in ms_kernels.cu; T = float: mixed precision, double: FP64).
+template <int NT, typename T>
 __global__ void __launch_bounds__(NT, 1) strip_sweep_kernel(const SweepArgs a) {
+  using V = typename StripT<T>::V;
   __shared__ RedSmem sm;
   __shared__ ResRed rred;
   __shared__ int s_task[2];
@@ -232,7 +306,7 @@ __global__ void __launch_bounds__(NT, 1) strip_sweep_kernel(const SweepArgs a) {
   const double* __restrict__ xin = (k & 1) ? a.xbuf1 : a.xbuf0;
   double* __restrict__ xout = (k & 1) ? a.xbuf0 : a.xbuf1;
   const bool residual_only = (k >= a.outer_maxit);
-  const CgVecs<float> v = slot_vecs<float>(a.scratch, a.vec_stride, slot);
+  const CgVecs<T> v = slot_vecs<T>(a.scratch, a.vec_stride, slot);
   const Geo G = a.g;
   const long long nxy = (long long)G.nx * G.ny;
   int par = 0;
@@ -252,26 +326,26 @@ __global__ void __launch_bounds__(NT, 1) strip_sweep_kernel(const SweepArgs a) {
       if (tid == 0) atomicOr(a.err, kErrGeometry);
       continue;
     }
-    const double scale = inner_scale<float>(a.inv_bnorm[tk.rhs]), unscale = 1.0 / scale;
+    const double scale = inner_scale<T>(a.inv_bnorm[tk.rhs]), unscale = 1.0 / scale;
     const long long rb = (long long)tk.rhs * G.npts;
     const double* __restrict__ xr = xin + rb;
     const double* __restrict__ fr = a.f ? a.f + rb : nullptr;
     const double* __restrict__ br = a.bnd ? a.bnd + (long long)tk.rhs * G.nbnd : nullptr;
-    // ---- 1. block residual in FP64, scaled, rounded to FP32 strips (padding lanes 0)
+    // ---- 1. block residual in FP64, scaled and rounded to T strips (padding lanes 0)
     double red0[2] = {0.0, 0.0};
     {
       double s_loc = 0.0;
-      float g_loc = 0.f;
+      T g_loc = T(0);
       for (int s0 = wbase; s0 < g.nstrips; s0 += NT) {
         const StripPos s = strip_pos(g, s0 + lane, lane);
         if (!s.has) continue;
         const int gy = tk.oy + s.y, gx0 = tk.ox + 4 * s.xs;
         for (int z = g.z0; z < g.z1; ++z) {
           const int gz = tk.oz + z;
-          float rv[4];
+          T rv[4];
 #pragma unroll
           for (int l = 0; l < 4; ++l) {
-            rv[l] = 0.f;
+            rv[l] = T(0);
             if (s.msk & (1u << l)) {
               const long long gi = (long long)gz * nxy + (long long)gy * G.nx + gx0 + l;
               double si, so;
@@ -279,10 +353,10 @@ __global__ void __launch_bounds__(NT, 1) strip_sweep_kernel(const SweepArgs a) {
               const double bh = fr ? fr[gi] + so : so;
               const double rr = bh - (6.0 * xr[gi] - si);
               if (owns(tk, 4 * s.xs + l, s.y, z)) s_loc += rr * rr;  // the global norm counts owned points
-              rv[l] = (float)(rr * scale);
+              rv[l] = (T)(rr * scale);
             }
           }
-          const float4 r = make_float4(rv[0], rv[1], rv[2], rv[3]);
+          const V r = StripT<T>::make(rv);
           st4(v.r + (long long)z * g.plane + s.off, r);
           g_loc += dot4f(r, r);
         }
@@ -297,8 +371,8 @@ __global__ void __launch_bounds__(NT, 1) strip_sweep_kernel(const SweepArgs a) {
     if (rank == 0 && tid == 0) a.partial[t] = sm.tot[0];
     if (residual_only) continue;
     // ---- 2. inner CG
-    const int m = strip_cg<NT>(v, g, (float)sm.tot[1], (float)sweep_inner_rtol(a, tk.rhs), a.inner_maxit, rred, rank,
-                               csize);
+    const int m = strip_cg<NT, T>(v, g, (T)sm.tot[1], (T)sweep_inner_rtol(a, tk.rhs), a.inner_maxit, rred, sm, rank,
+                                  csize);
     // ---- 3. outer update into the other buffer (owned points only)
     double* __restrict__ xo = xout + rb;
     for (int s0 = wbase; s0 < g.nstrips; s0 += NT) {
@@ -307,8 +381,8 @@ __global__ void __launch_bounds__(NT, 1) strip_sweep_kernel(const SweepArgs a) {
       const int gy = tk.oy + s.y, gx0 = tk.ox + 4 * s.xs;
       for (int z = g.z0; z < g.z1; ++z) {
         const long long gi0 = (long long)(tk.oz + z) * nxy + (long long)gy * G.nx + gx0;
-        const float4 d = m > 0 ? ld4(v.d + (long long)z * g.plane + s.off) : zero4();
-        const float dv[4] = {d.x, d.y, d.z, d.w};
+        const V d = m > 0 ? ld4(v.d + (long long)z * g.plane + s.off) : StripT<T>::zero();
+        const T dv[4] = {d.x, d.y, d.z, d.w};
 #pragma unroll
         for (int l = 0; l < 4; ++l)
           if ((s.msk & (1u << l)) && owns(tk, 4 * s.xs + l, s.y, z)) xo[gi0 + l] = xr[gi0 + l] + (double)dv[l] * unscale;
@@ -323,9 +397,9 @@ __global__ void __launch_bounds__(NT, 1) strip_sweep_kernel(const SweepArgs a) {
 }
 
 // ---------------------------------------------------------------- launchers
-template <int NT>
+template <int NT, typename T>
 static cudaError_t prep_strip(int cluster, void** fn) {
-  auto kern = strip_sweep_kernel<NT>;
+  auto kern = strip_sweep_kernel<NT, T>;
   if (cluster > 8) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
@@ -334,10 +408,17 @@ static cudaError_t prep_strip(int cluster, void** fn) {
   return cudaSuccess;
 }
 
-static cudaError_t strip_fn(int threads, int cluster, void** fn) {
-  if (threads == 256) return prep_strip<256>(cluster, fn);
-  if (threads == 512) return prep_strip<512>(cluster, fn);
-  if (threads == 1024) return prep_strip<1024>(cluster, fn);
+// prec: 1 mixed (FP32 inner solve), 0 FP64
+static cudaError_t strip_fn(int prec, int threads, int cluster, void** fn) {
+  if (prec == 1) {
+    if (threads == 256) return prep_strip<256, float>(cluster, fn);
+    if (threads == 512) return prep_strip<512, float>(cluster, fn);
+    if (threads == 1024) return prep_strip<1024, float>(cluster, fn);
+  } else {
+    if (threads == 256) return prep_strip<256, double>(cluster, fn);
+    if (threads == 512) return prep_strip<512, double>(cluster, fn);
+    if (threads == 1024) return prep_strip<1024, double>(cluster, fn);
+  }
   return cudaErrorInvalidValue;
 }
 
@@ -355,9 +436,9 @@ static void strip_cfg(cudaLaunchConfig_t* cfg, cudaLaunchAttribute* at, int thre
   cfg->numAttrs = 1;
 }
 
-cudaError_t strip_max_clusters(int threads, int cluster, int* out) {
+cudaError_t strip_max_clusters(int prec, int threads, int cluster, int* out) {
   void* fn = nullptr;
-  cudaError_t e = strip_fn(threads, cluster, &fn);
+  cudaError_t e = strip_fn(prec, threads, cluster, &fn);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute at[1];
@@ -365,9 +446,9 @@ cudaError_t strip_max_clusters(int threads, int cluster, int* out) {
   return cudaOccupancyMaxActiveClusters(out, fn, &cfg);
 }
 
-cudaError_t launch_strip_sweep(int threads, int cluster, int slots, const SweepArgs& a, cudaStream_t s) {
+cudaError_t launch_strip_sweep(int prec, int threads, int cluster, int slots, const SweepArgs& a, cudaStream_t s) {
   void* fn = nullptr;
-  cudaError_t e = strip_fn(threads, cluster, &fn);
+  cudaError_t e = strip_fn(prec, threads, cluster, &fn);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute at[1];

@@ -137,19 +137,19 @@ int list_shapes(Tuner& t, int prec, int mode, int engine, const std::vector<Task
     if (engine == 2) return out->empty() ? (int)cudaErrorInvalidConfiguration : 0;
   }
   int last = 0;
-  if (prec == 1 && mode == 0) {
-    // vectorised streaming candidates (FP32, sync): same slot model as the scalar engine
+  if (mode == 0) {
+    // vectorised streaming candidates (sync; FP32 inner solve or FP64): same slot model as the scalar engine
     for (int threads : {512, 1024}) {
       if (req_threads && req_threads != threads) continue;
       LaunchShape s;
       if (streaming_shape(t, prec, mode, tasks, maxpts, req_cluster, 0, req_slots, threads, &s) != 0) continue;
       int occ = 0;
-      auto key = std::make_tuple(300, 0, threads, s.cluster);
+      auto key = std::make_tuple(300 + prec, 0, threads, s.cluster);
       auto it = t.occ.find(key);
       if (it != t.occ.end()) {
         occ = it->second;
       } else {
-        if (strip_max_clusters(threads, s.cluster, &occ) != cudaSuccess) {
+        if (strip_max_clusters(prec, threads, s.cluster, &occ) != cudaSuccess) {
           cudaGetLastError();
           occ = 0;
         }

@@ -47,11 +47,11 @@ def test_ctypes_structs_match_c_layout(tmp_path):
 #include <stddef.h>
 #include "ms.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(ms_opts), offsetof(ms_opts, outer_tol),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(ms_opts), offsetof(ms_opts, outer_tol),
          offsetof(ms_opts, res_hist), offsetof(ms_opts, slow_ns), offsetof(ms_opts, time_limit_ms),
          offsetof(ms_opts, variant), offsetof(ms_opts, inner_adapt), offsetof(ms_opts, overlap),
          offsetof(ms_opts, gmres_restart), offsetof(ms_opts, wait_polls), offsetof(ms_opts, trace_cap),
-         offsetof(ms_opts, trace));
+         offsetof(ms_opts, trace), offsetof(ms_opts, sum_polls));
   printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(ms_stats), offsetof(ms_stats, lups), offsetof(ms_stats, per_rhs_rel),
          offsetof(ms_stats, slots), offsetof(ms_stats, variant), offsetof(ms_stats, inner_rtol_final),
          offsetof(ms_stats, trace_count));
@@ -68,7 +68,8 @@ int main(void) {
     assert [int(v) for v in a.split()] == [ctypes.sizeof(O), O.outer_tol.offset, O.res_hist.offset,
                                           O.slow_ns.offset, O.time_limit_ms.offset, O.variant.offset,
                                           O.inner_adapt.offset, O.overlap.offset, O.gmres_restart.offset,
-                                          O.wait_polls.offset, O.trace_cap.offset, O.trace.offset]
+                                          O.wait_polls.offset, O.trace_cap.offset, O.trace.offset,
+                                          O.sum_polls.offset]
     assert [int(v) for v in b.split()] == [ctypes.sizeof(S), S.lups.offset, S.per_rhs_rel.offset, S.slots.offset,
                                           S.variant.offset, S.inner_rtol_final.offset, S.trace_count.offset]
     from paper_2009_12638_gb300 import TRACE_DTYPE
@@ -85,7 +86,7 @@ def test_default_opts(lib):
     assert o.slow_block == -1 and o.use_graph == 1
     assert o.variant == -1 and o.inner_adapt == 0 and o.overlap == 0
     assert o.inner_method == 0 and o.gmres_restart == 10
-    assert o.wait_polls == 0 and o.trace_cap == 0 and not o.trace
+    assert o.wait_polls == 0 and o.trace_cap == 0 and not o.trace and o.sum_polls == 0
 
 
 def test_resident_variant_table(lib):
@@ -161,7 +162,8 @@ def test_solve_rejects_bad_arguments_before_device_work(lib):
         dummy = ctypes.c_void_p(16)  # never dereferenced: options are checked first
         for field, value in [("mode", 7), ("precision", 3), ("inner_maxit", -1), ("threads", 100),
                              ("cluster", 17), ("outer_tol", -1.0), ("time_limit_ms", -5.0), ("variant", -2),
-                             ("variant", 10000), ("inner_adapt", 2), ("overlap", -1), ("inner_method", 2)]:
+                             ("variant", 10000), ("inner_adapt", 2), ("overlap", -1), ("inner_method", 2),
+                             ("sum_polls", -1)]:
             o2 = _lib.Opts()
             lib.ms_default_opts(ctypes.byref(o2))
             setattr(o2, field, value)

@@ -97,6 +97,15 @@ def first_sweeps_case(nx, ny, nz, cx, cy, cz, nrhs, sweeps, seed, f=False, x0=Fa
         assert rel_inf(xg[s], ref["x"]) <= 1e-11, s
 
 
+@pytest.mark.parametrize("threads", [256, 512, 1024])
+def test_fp64_first_sweeps_on_both_streaming_engines(threads):
+    """The plain FP64 path runs on the scalar streaming engine (256 threads
+    here) or on the vectorised strip engine in FP64 (512 / 1024 threads: 4-point
+    strips of doubles, FP64 cluster sums): both must give the oracle's sweeps."""
+    first_sweeps_case(64, 48, 40, [0, 40, 64], [0, 17, 48], [0, 13, 27, 40], 2, 3, 22, f=True, x0=True,
+                      engine="streaming", threads=threads)
+
+
 @pytest.mark.parametrize("case", [
     # (nx, ny, nz, cx, cy, cz): several tiles, ragged tails, thin and single blocks
     (37, 29, 23, [0, 13, 37], [0, 10, 20, 29], [0, 23]),
@@ -150,6 +159,24 @@ def test_exact_start_stops_at_k0():
     x, st = g.solve(bnd=cuda(bnd), x0=cuda(x0), precision="mixed")
     assert st.status == 0 and st.outer_its == 0
     np.testing.assert_array_equal(x.cpu().numpy(), x0)
+
+
+@pytest.mark.parametrize("prec,threads", [("fp64", 512), ("fp64", 1024), ("mixed", 512), ("mixed", 1024)])
+@pytest.mark.parametrize("case", [(6, 6, 6, [0, 3, 6], [0, 6], [0, 6]), (8, 8, 8, [0, 4, 8], [0, 8], [0, 8]),
+                                  (13, 7, 9, [0, 1, 5, 9, 13], [0, 7], [0, 4, 9])])
+def test_strip_engine_blocks_one_strip_wide(case, prec, threads):
+    """Blocks at most 4 points wide hold one x-strip per row: the strip
+    engine's strip-to-row mapping must stay exact there (the relative residual
+    of x0 = 0 is 1, and two sweeps are the oracle's)."""
+    nx, ny, nz, cx, cy, cz = case
+    bnd = np.random.default_rng(28).uniform(-1, 1, size=(1, inputs.boundary_size(nx, ny, nz)))
+    g = make_grid(nx, ny, nz, 1, cx, cy, cz)
+    shape = dict(precision=prec, engine="streaming", threads=threads)
+    x, st = g.solve(bnd=cuda(bnd), outer_maxit=0, history=True, **shape)
+    assert st.history[0][0] == pytest.approx(1.0, rel=1e-12)
+    x, st = g.solve(bnd=cuda(bnd), outer_tol=0.0, outer_maxit=2, **shape)
+    ref = oracle.solve(nx, ny, nz, cx, cy, cz, bnd=bnd[0], outer_tol=0.0, outer_maxit=2)
+    assert rel_inf(x.cpu().numpy()[0], ref["x"]) <= (1e-11 if prec == "fp64" else 2e-4)
 
 
 def test_outer_maxit_zero():
@@ -215,6 +242,9 @@ def test_solve_host_matches_device():
     c = inputs.equal_cuts(n, 2)
     bnd = inputs.boundary_uniform(n, n, n, 2, 31)
     g = make_grid(n, n, n, 2, c, c, c)
+    # tune the launch shape first: the tuning sweeps try several engines, whose
+    # FP64 sums round differently; the two solves compared below use one shape
+    g.solve(bnd=cuda(bnd), precision="fp64")
     xd, sd = g.solve(bnd=cuda(bnd), precision="fp64")
     xh = np.zeros((2, n, n, n))
     xh, sh = g.solve_host(bnd=bnd, x=xh, precision="fp64")
@@ -289,6 +319,29 @@ def test_persistent_wait_budget_runs_out_returns_timeout():
     assert g.residual(x, bnd=b)[0] == pytest.approx(st.rel_residual, rel=1e-12)
     x2, s2 = g.solve(bnd=b, slow_block=5, slow_ns=100_000, **shape)
     assert s2.status == 0 and s2.rel_residual < 1e-8
+
+
+@pytest.mark.parametrize("mode,persistent", [("sync", False), ("sync", True), ("async", False)])
+def test_tagged_sum_wait_runs_out_returns_timeout(mode, persistent):
+    """The resident CG forms p.Ap without a cluster barrier: each CTA polls for
+    the other CTAs' tagged totals, a wait bounded by opts.sum_polls.  With a
+    budget of one poll the wait runs out (a total takes far longer than one
+    poll to arrive from another SM): the solve must end by itself with
+    MS_ERR_TIMEOUT in every launch form (no CTA leaves the CG loop or a
+    cluster barrier out of step with the others), and the GPU stays usable --
+    the same solve with the default budget converges."""
+    import time
+    cfg = inputs.make_config("laplace256_u11", scale=4)
+    g = make_grid(cfg["nx"], cfg["ny"], cfg["nz"], 1, cfg["cx"], cfg["cy"], cfg["cz"])
+    b = cuda(cfg["bnd"])
+    shape = dict(cluster=4, threads=512, precision="mixed", engine="resident", mode=mode, persistent=persistent)
+    t0 = time.perf_counter()
+    x, st = g.solve(bnd=b, sum_polls=1, outer_maxit=20, outer_tol=0.0, **shape)
+    assert time.perf_counter() - t0 < 30.0
+    assert st.status == 5
+    x2, s2 = g.solve(bnd=b, **shape)
+    assert s2.status == 0 and s2.rel_residual < 1e-8
+    assert g.residual(x2, bnd=b)[0] < 1e-8
 
 
 def test_sync_time_limit_returns_timeout():
