@@ -494,7 +494,6 @@ extern "C" int ms_sweep(ms_grid* g, const double* f, const double* bnd, const do
   MS_CUDA(g, g->ctl.reserve(L.bytes));
   char* ctlb = g->ctl.as<char>();
   Ctl* ctl = reinterpret_cast<Ctl*>(ctlb);
-  double* norms = reinterpret_cast<double*>(ctlb + L.off_norm);
   double* invb = reinterpret_cast<double*>(ctlb + L.off_invb);
   unsigned long long* inner = reinterpret_cast<unsigned long long*>(ctlb + L.off_inner);
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
