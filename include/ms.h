@@ -256,7 +256,12 @@ MS_API int ms_norms(ms_grid* grid, const double* f, const double* bnd, const dou
  *   stats:  HOST or NULL.  NULL: nothing waits for the GPU (the results are
  *           ready on `stream`'s timeline).  Non-NULL: synchronises `stream` and
  *           fills inner_its, lups, time_ms, the launch shape, outer_its = 1 and
- *           rel_residual = that of x^k against this grid's own ||bhat||.
+ *           rel_residual = that of x^k against this grid's own ||bhat||;
+ *           returns MS_ERR_TIMEOUT (stats->status too) if a bounded device
+ *           wait of the sweep ran out (opts.sum_polls), the result then not
+ *           to be used.
+ * Returns MS_OK, MS_ERR_ARG (NULL or overlapping buffers, invalid options,
+ * a mode other than sync), MS_ERR_CUDA or MS_ERR_TIMEOUT (above).
  * The launch shape is the one a solve of the same problem measured (ms_solve
  * caches it per handle), else the model's first choice.  The inner solves use
  * the same kernels and FP32 scaling as ms_solve, so a sweep here equals a
