@@ -79,6 +79,19 @@ def test_batched_uneven_first_sweep_sampled_rhs():
         assert rel_inf(xs[s], ref["x"]) <= 2e-4, s
 
 
+def test_batched_uneven_first_sweep_fp64_sampled_rhs():
+    """The plain FP64 path on the uneven blocks (ragged x-strips: edges that are
+    not multiples of 4), in the launch shape the model picks for it (the
+    vectorised streaming engine on FP64 strips): one sweep of every rhs, one
+    sampled rhs against the oracle."""
+    cfg = inputs.make_config("batched_uneven")
+    g = grid_for(cfg)
+    x, st = g.solve(bnd=torch.from_numpy(cfg["bnd"]).cuda(), precision="fp64", outer_tol=0.0, outer_maxit=1)
+    assert st.outer_its == 1
+    ref = oracle_sweeps(cfg, 7, 1)
+    assert rel_inf(x.cpu().numpy()[7], ref["x"]) <= 1e-11
+
+
 def test_laplace512_first_sweep_sampled_rhs():
     cfg = inputs.make_config("laplace512_async")
     g = grid_for(cfg)
