@@ -128,7 +128,9 @@ __global__ void __launch_bounds__(NT, 1) sweep_kernel(const SweepArgs a) {
 __device__ __forceinline__ int adapt_rung_of(const AdaptState& st, int j) {
   if (j < st.rs || j >= st.rs + 3 * kAdaptWindow) return st.c;
   const int w = (j - st.rs) / kAdaptWindow;
-  const int r = st.c + (w == 1 ? -1 : (w == 2 ? 1 : 0));
+  int r = st.c + (w == 1 ? -1 : (w == 2 ? 1 : 0));
+  if (r < 0) r = st.c + kAdaptEdgeProbe;
+  else if (r >= kAdaptRungs) r = st.c - kAdaptEdgeProbe;
   return r < 0 ? 0 : (r >= kAdaptRungs ? kAdaptRungs - 1 : r);
 }
 
@@ -143,8 +145,10 @@ __device__ void adapt_step(const CheckArgs& a, int s, int k, double rho) {
     const int j = k - 1;
     if (j >= st.rs && j < st.rs + 3 * kAdaptWindow) {
       const int w = (j - st.rs) / kAdaptWindow;
-      st.acc_d[w] += st.lr_prev - lr;
-      st.acc_w[w] += st.cum_prev - st.cum_prev2;
+      if ((j - st.rs) % kAdaptWindow >= kAdaptSkip) {
+        st.acc_d[w] += st.lr_prev - lr;
+        st.acc_w[w] += st.cum_prev - st.cum_prev2;
+      }
       if (j == st.rs + 3 * kAdaptWindow - 1) {
         int best = 0;
         double be = -1e300;
