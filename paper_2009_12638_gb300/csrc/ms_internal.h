@@ -90,20 +90,14 @@ __host__ __device__ inline double sweep_inner_rtol(const SweepArgs& a, int rhs) 
 // Runtime adaptation of the inner tolerance (opts.inner_adapt), per rhs, run
 // by the check kernel after every sweep.  A ladder of relative inner
 // tolerances; rounds of 3 x kAdaptWindow sweeps run the centre rung, the next
-// looser and the next tighter one (at an end of the ladder, where that
-// neighbour does not exist, the rung kAdaptEdgeProbe steps inward instead, so
-// that a search walked to an end by the first rounds can leave it); each
-// sweep's decrease of log(rho) is charged to the rung it ran with, against
-// its work (inner lattice updates plus kAdaptSweepCost x points for the
-// residual and update), except the first kAdaptSkip sweeps of a window, whose
-// decrease still reflects the residual the previous rung left; the rung with
+// looser and the next tighter one; each sweep's decrease of log(rho) is
+// charged to the rung it ran with, against its work (inner lattice updates
+// plus kAdaptSweepCost x points for the residual and update); the rung with
 // the largest decrease per work becomes the centre of the next round.  Every
 // input is deterministic (residuals and iteration counts, no clocks).
 constexpr int kAdaptRungs = 11;
 constexpr int kAdaptStart = 3;        // rung of the first sweeps (0.3)
 constexpr int kAdaptWindow = 8;       // sweeps per rung and round
-constexpr int kAdaptSkip = 2;         // sweeps at the start of a window that are not charged
-constexpr int kAdaptEdgeProbe = 4;    // inward distance of the probe at an end of the ladder
 constexpr int kAdaptWarmup = 4;       // sweeps before the first round
 constexpr double kAdaptSweepCost = 12.0;  // residual + update, in inner iterations per point
 __host__ __device__ inline double adapt_rung_rtol(int r) {

@@ -124,6 +124,15 @@ __global__ void __launch_bounds__(NT, 1) sweep_kernel(const SweepArgs a) {
   }
 }
 
+// Two guards on the controller's local search.  The first kAdaptSkip sweeps
+// of a window are not charged: their decrease of log(rho) still reflects the
+// residual the previous rung left.  At an end of the ladder, where the looser
+// or tighter neighbour does not exist, its window runs the rung
+// kAdaptEdgeProbe steps inward, so that a search walked to an end by the
+// first rounds can leave it.
+constexpr int kAdaptSkip = 2;
+constexpr int kAdaptEdgeProbe = 4;
+
 // Rung of sweep j under the round schedule of `st` (see AdaptState).
 __device__ __forceinline__ int adapt_rung_of(const AdaptState& st, int j) {
   if (j < st.rs || j >= st.rs + 3 * kAdaptWindow) return st.c;
