@@ -121,8 +121,9 @@ typedef struct {
                             residual and update), tries the neighbouring tolerances of a ladder
                             (0.8 ... 1e-3) in rounds of 8 sweeps each (the first 2 of a window not
                             charged; at an end of the ladder the rung 4 steps inward instead of the
-                            missing neighbour) and keeps the most efficient; inner_maxit still caps
-                            every inner solve.  Deterministic (no clocks). */
+                            missing neighbour; each rung's charges kept across rounds, halved per
+                            round) and keeps the most efficient; inner_maxit still caps every inner
+                            solve.  Deterministic (no clocks). */
   int overlap;           /* sync mode: overlapping blocks (section 3.2), o >= 0 points per face
                             (default 0).  Block i solves on its box extended by o points on every
                             face (clipped to the grid) with zero Dirichlet data outside the box;

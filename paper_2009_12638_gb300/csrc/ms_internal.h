@@ -90,14 +90,24 @@ __host__ __device__ inline double sweep_inner_rtol(const SweepArgs& a, int rhs) 
 // Runtime adaptation of the inner tolerance (opts.inner_adapt), per rhs, run
 // by the check kernel after every sweep.  A ladder of relative inner
 // tolerances; rounds of 3 x kAdaptWindow sweeps run the centre rung, the next
-// looser and the next tighter one; each sweep's decrease of log(rho) is
-// charged to the rung it ran with, against its work (inner lattice updates
-// plus kAdaptSweepCost x points for the residual and update); the rung with
-// the largest decrease per work becomes the centre of the next round.  Every
-// input is deterministic (residuals and iteration counts, no clocks).
+// looser and the next tighter one (at an end of the ladder, where that
+// neighbour does not exist, the rung kAdaptEdgeProbe steps inward instead, so
+// that a search walked to an end by the first rounds can leave it); each
+// sweep's decrease of log(rho) is charged to the rung it ran with, against
+// its work (inner lattice updates plus kAdaptSweepCost x points for the
+// residual and update), except the first kAdaptSkip sweeps of a window, whose
+// decrease still reflects the residual the previous rung left.  Every rung
+// keeps its charges across rounds, scaled by kAdaptMemory at each round's end,
+// so that a rung's rate rests on more than one window; of the round's three
+// rungs the one with the largest decrease per work becomes the centre of the
+// next round.  Every input is deterministic (residuals and iteration counts,
+// no clocks).
 constexpr int kAdaptRungs = 11;
 constexpr int kAdaptStart = 3;        // rung of the first sweeps (0.3)
 constexpr int kAdaptWindow = 8;       // sweeps per rung and round
+constexpr int kAdaptSkip = 2;         // sweeps at the start of a window that are not charged
+constexpr int kAdaptEdgeProbe = 4;    // inward distance of the probe at an end of the ladder
+constexpr double kAdaptMemory = 0.5;  // weight of a rung's earlier charges after each round
 constexpr int kAdaptWarmup = 4;       // sweeps before the first round
 constexpr double kAdaptSweepCost = 12.0;  // residual + update, in inner iterations per point
 __host__ __device__ inline double adapt_rung_rtol(int r) {
@@ -111,6 +121,8 @@ struct AdaptState {
   double lr_prev;              // log(rho_{k-1})
   double cum_prev, cum_prev2;  // cumulative work at checks k-1 and k-2
   double acc_d[3], acc_w[3];   // round sums per window: log-residual decrease, work
+  double mem_d[kAdaptRungs];   // per rung: charges of earlier rounds, scaled by kAdaptMemory per round
+  double mem_w[kAdaptRungs];
 };
 
 struct CheckArgs {

@@ -124,15 +124,6 @@ __global__ void __launch_bounds__(NT, 1) sweep_kernel(const SweepArgs a) {
   }
 }
 
-// Two guards on the controller's local search.  The first kAdaptSkip sweeps
-// of a window are not charged: their decrease of log(rho) still reflects the
-// residual the previous rung left.  At an end of the ladder, where the looser
-// or tighter neighbour does not exist, its window runs the rung
-// kAdaptEdgeProbe steps inward, so that a search walked to an end by the
-// first rounds can leave it.
-constexpr int kAdaptSkip = 2;
-constexpr int kAdaptEdgeProbe = 4;
-
 // Rung of sweep j under the round schedule of `st` (see AdaptState).
 __device__ __forceinline__ int adapt_rung_of(const AdaptState& st, int j) {
   if (j < st.rs || j >= st.rs + 3 * kAdaptWindow) return st.c;
@@ -159,18 +150,27 @@ __device__ void adapt_step(const CheckArgs& a, int s, int k, double rho) {
         st.acc_w[w] += st.cum_prev - st.cum_prev2;
       }
       if (j == st.rs + 3 * kAdaptWindow - 1) {
+        for (int r = 0; r < kAdaptRungs; ++r) {
+          st.mem_d[r] *= kAdaptMemory;
+          st.mem_w[r] *= kAdaptMemory;
+        }
+        int rq[3];
+        for (int q = 0; q < 3; ++q) {
+          rq[q] = adapt_rung_of(st, st.rs + q * kAdaptWindow);
+          st.mem_d[rq[q]] += st.acc_d[q];
+          st.mem_w[rq[q]] += st.acc_w[q];
+        }
         int best = 0;
         double be = -1e300;
         for (int q = 0; q < 3; ++q) {
-          const double e = st.acc_w[q] > 0.0 ? st.acc_d[q] / st.acc_w[q] : -1e300;
+          const double e = st.mem_w[rq[q]] > 0.0 ? st.mem_d[rq[q]] / st.mem_w[rq[q]] : -1e300;
           if (e > be) {
             be = e;
             best = q;
           }
         }
-        const int rbest = adapt_rung_of(st, st.rs + best * kAdaptWindow);
         for (int q = 0; q < 3; ++q) st.acc_d[q] = st.acc_w[q] = 0.0;
-        st.c = rbest;
+        st.c = rq[best];
         st.rs = k + 1;
       }
     }
